@@ -1,0 +1,30 @@
+"""ORACLE -- test infrastructure only.
+
+A plain, slow, FP64 CPU implementation of the non-recursive N-dimensional
+Bartels-Stewart method (Cuesta & de la Hoz, arXiv 2412.15840).  Only the tests,
+`__graft_entry__.smoke()` and the CPU-baseline / reference leg of `bench.py` may
+import it.  The CUDA library shares no code with it and never calls it.
+
+Pinned by the `-m "not gpu"` tests in tests/test_oracle.py against: the
+worked index example of Section 3 (golden fixture), a dense solve of the
+Kronecker-sum system of Eq. (systvec), the classical 2-D Sylvester solver
+(Eq. (sylvester)), the FFT closed form for circulant operators and the
+diagonal closed form (Remark 1), the singleton reduction, the residual
+invariant, the nested-loop Algorithm 1, and planted mistakes.
+"""
+from .bartels_stewart import (  # noqa: F401
+    linear_index,
+    counter_order,
+    mode_product,
+    apply_operator,
+    residual,
+    schur_factors,
+    forward_transform,
+    triangular_sweep,
+    triangular_sweep_nested,
+    back_transform,
+    solve,
+    solve_with_factors,
+    rel_err,
+    backward_error,
+)
