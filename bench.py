@@ -1,0 +1,337 @@
+"""Benchmark: solved entries/s of the N-dimensional Sylvester solver on GB300.
+
+Workload (one step = one full solve, all hot-path phases): N=4, n_k=64
+(16,777,216 complex entries, 268 MB per complex128 tensor), operators
+A_k = (randn + i randn)/8 + 3I, complex Gaussian B, seed = rank.  The headline
+`value` is the mixed path (FP32 transforms and sweep, FP64 residual and
+update, refinement to 1e-10 relative error); the plain FP64 path is reported
+beside it.  The Schur setup (plan creation) is outside the timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun each rank solves its own equation (independent problems, weak
+scaling); timings are the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import sylv_inputs as si  # noqa: E402
+
+METRIC = "entries solved/s, FP64 vs mixed+refine at 1e-10 rel err; % of roofline"
+UNIT = "entries/s"
+SHAPE = (64, 64, 64, 64)
+RTOL = 1e-10
+MAX_REFINE = 3
+
+# FP64 FMA pipe: 2 FP64 FMA per clock per SM (152 SMs) at the 2070 MHz
+# maximum SM clock -> 152 * 2 * 2 * 2.07e9 = 1.2586e12 FLOP/s
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+
+# DRAM traffic per launch of the FP64 residual pass kernel, from an ncu capture
+# (see profiles/); valid only for the kernel source it was measured on.
+TRAFFIC = {"kernels_sha": None, "bytes_per_launch": None}
+
+
+def kernels_sha() -> str:
+    p = os.path.join(ROOT, "paper_2412_15840_gb300", "csrc", "kernels.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-oracle", action="store_true",
+                    help="skip the oracle error check and CPU baseline")
+    return ap.parse_args()
+
+
+def oracle_threads() -> int:
+    try:
+        from threadpoolctl import threadpool_info
+        return max([d.get("num_threads", 1) for d in threadpool_info()] + [1])
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# --------------------------------------------------------------- clocks ----
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+        self.active = False
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.device)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            if self.active:
+                self.lines.append(line.strip())
+
+    def mark(self, on: bool):
+        self.active = on
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = [l.split(", ") for l in self.lines if l.count(",") >= 8]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        pw = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "power_w_max": max(pw) if pw else None, "samples": len(rows)}
+
+
+# ------------------------------------------------------------- reference ---
+
+def run_reference(args, rank: int, world: int):
+    """The oracle as it stands, on the host cores: one full solve per step."""
+    if rank != 0:
+        return 0
+    import oracle
+    p = si.random_problem(SHAPE, 1, seed=0, name="N4_n64")
+    entries = p.n_tot * p.nrhs
+    for _ in range(args.warmup):
+        oracle.solve(p.A, p.B)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.solve(p.A, p.B)
+    dt = time.perf_counter() - t0
+    value = entries * args.steps / dt
+    cores = oracle_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+        "data": "synthetic", "config": config_block(),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "one full CPU-oracle solve of the N=4, n=64 workload per "
+                                   "step (numpy/BLAS transforms, single-thread C sweep)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def config_block():
+    return {"workload": "N4_n64: N=4, n_k=64, 16,777,216 complex entries, 1 RHS, "
+                        "A_k=(randn+i randn)/8+3I, seed=rank",
+            "N": 4, "n": 64, "nrhs": 1, "entries": 64 ** 4, "rtol": RTOL,
+            "prec_headline": "mixed_fp32 (FP32 solve + FP64 residual refinement)",
+            "l2": "inputs larger than L2 (268 MB complex128 tensors, 129 MB L2)"}
+
+
+# ------------------------------------------------------------------- ours --
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+
+    from paper_2412_15840_gb300.build import build
+    build()
+    from paper_2412_15840_gb300 import Plan, from_device
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    p = si.random_problem(SHAPE, 1, seed=rank, name="N4_n64")
+    entries = p.n_tot * p.nrhs
+    flat = p.B.reshape(-1, order="F")
+    B_host = torch.from_numpy(flat).pin_memory()
+    B = B_host.to(dev)
+    X = torch.empty_like(B)
+
+    t0 = time.perf_counter()
+    mixed = Plan(A=p.A, nrhs=1, prec="mixed", rtol=RTOL, max_refine=MAX_REFINE, device=local)
+    setup_s_mixed = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    fp64 = Plan(A=p.A, nrhs=1, prec="fp64", device=local)
+    setup_s_fp64 = time.perf_counter() - t0
+    ws_m = mixed.workspace()
+    ws_f = fp64.workspace()
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, k, sampler=None):
+        barrier()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        if sampler:
+            sampler.mark(True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if sampler:
+            sampler.mark(False)
+        barrier()
+        return max_over_ranks(e0.elapsed_time(e1) / k)
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.5)
+
+    # --- headline: mixed path, device-resident inputs
+    def step_mixed():
+        mixed.solve(B, X, workspace=ws_m, stream=stream)
+
+    for _ in range(args.warmup):
+        step_mixed()
+    mixed.set_timing(True)
+    ms_mixed = timed(step_mixed, args.steps, sampler)
+    mixed.set_timing(False)
+    phases_m = mixed.timing(reset=True)
+    X_mixed, info_m = mixed.solve(B, X, workspace=ws_m, stream=stream, info=True)
+    X_mixed_host = from_device(X_mixed, p.B.shape) if rank == 0 else None
+
+    # --- plain FP64 path
+    X64 = torch.empty_like(B)
+
+    def step_fp64():
+        fp64.solve(B, X64, workspace=ws_f, stream=stream)
+
+    for _ in range(args.warmup):
+        step_fp64()
+    fp64.set_timing(True)
+    ms_fp64 = timed(step_fp64, args.steps, sampler)
+    fp64.set_timing(False)
+    phases_f = fp64.timing(reset=True)
+    _, info_f = fp64.solve(B, X64, workspace=ws_f, stream=stream, info=True)
+    X_fp64_host = from_device(X64, p.B.shape) if rank == 0 else None
+
+    # --- end to end through the C ABI: pinned host B -> device, solve, X -> host
+    X_host = torch.empty_like(B_host).pin_memory()
+
+    def step_e2e():
+        B.copy_(B_host, non_blocking=True)
+        mixed.solve(B, X, workspace=ws_m, stream=stream)
+        X_host.copy_(X, non_blocking=True)
+
+    for _ in range(args.warmup):
+        step_e2e()
+    ms_e2e = timed(step_e2e, args.steps, sampler)
+    clocks = sampler.stop()
+
+    value = world * entries / (ms_mixed * 1e-3)
+    value_fp64 = world * entries / (ms_fp64 * 1e-3)
+    value_e2e = world * entries / (ms_e2e * 1e-3)
+    nbytes = entries * 16
+
+    # roofline of the dominant kernel (FP64 residual passes of the mixed path)
+    solves = max(1, phases_m["solves"])
+    iters = max(1, info_m["refine_iters"])
+    sum_n = sum(n for n in SHAPE if n > 1)
+    res_flops_per_pass = 8.0 * entries * sum_n            # one residual over all modes
+    res_ms = phases_m["ms"]["residual"] / solves          # per solve (all iterations)
+    achieved = res_flops_per_pass * iters / (res_ms * 1e-3) / 1e12 if res_ms > 0 else None
+    traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["kernels_sha"] == kernels_sha() else None
+    top_phase = max(("forward", "sweep", "back", "residual", "update"),
+                    key=lambda k: phases_m["ms"][k])
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_mixed, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "fp32+fp64 (c64 solve, c128 residual)",
+        "data": "synthetic", "config": config_block(),
+        "fp64": {"value": value_fp64, "unit": UNIT, "ms_per_step": ms_fp64, "dtype": "c128"},
+        "speedup_mixed_over_fp64": value / value_fp64,
+        "refine_iters": info_m["refine_iters"], "est_rel_err": info_m["est_rel_err"],
+        "e2e": {"value": value_e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                "d2h_bytes_per_step": nbytes, "ms_per_step": ms_e2e},
+        "gpu_launches": int(info_m["launches"]) * args.steps,
+        "roofline": {"bound": "alu", "kernel": "k_modeprod<double,...,EPI_RESID> (FP64 residual)",
+                     "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
+                     "traffic": traffic,
+                     "peak_note": "FP64 FMA pipe derived: 152 SMs x 2 FMA/clk x 2 FLOP x 2070 MHz"},
+        "phases_ms_per_solve": {
+            "mixed": {k: v / solves for k, v in phases_m["ms"].items()},
+            "fp64": {k: v / max(1, phases_f["solves"]) for k, v in phases_f["ms"].items()}},
+        "top_phase_mixed": top_phase,
+        "setup_s": {"mixed": setup_s_mixed, "fp64": setup_s_fp64},
+        "clocks": clocks,
+    }
+
+    if rank == 0 and not args.no_oracle:
+        import oracle
+        t0 = time.perf_counter()
+        Xo = oracle.solve(p.A, p.B)
+        dt = time.perf_counter() - t0
+        line["rel_err_vs_oracle"] = {"mixed": oracle.rel_err(X_mixed_host, Xo),
+                                     "fp64": oracle.rel_err(X_fp64_host, Xo)}
+        line["cpu_baseline"] = {
+            "value": entries / dt, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
+            "sample": "one full CPU-oracle solve of this rank-0 N=4, n=64 equation "
+                      "(numpy/BLAS transforms, single-thread C sweep); " f"{dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,207 @@
+/*
+ * sylv.h -- C ABI of the GB300 (sm_103a) solver for the N-dimensional
+ * Sylvester tensor equation
+ *
+ *     sum_{j=1..N} A_j (x)_j X = B,
+ *     [A (x)_j X]_{i_1..i_j..i_N} = sum_k a_{i_j k} x_{i_1..k..i_N}
+ *
+ * (Cuesta & de la Hoz, arXiv 2412.15840, Section 1, Eq. (sylvesterND)), by the
+ * non-recursive Bartels-Stewart method of Section 2 / Algorithm 3:
+ *   setup    A_j = U_j T_j U_j^*  (complex Schur, host FP64, once per plan);
+ *   forward  C = U_N^* (x)_N ( ... (U_1^* (x)_1 B))        Eq. (CUNU2U1B);
+ *   sweep    sum_j T_j (x)_j Y = C solved entrywise         Eq. (yi1i2iN);
+ *   back     X = U_N (x)_N ( ... (U_1 (x)_1 Y))           Eq. (XUNU2U1Y).
+ *
+ * Conventions shared by every entry point
+ *  - Complex numbers are interleaved (re, im) pairs: complex128 = 2 doubles,
+ *    complex64 = 2 floats.
+ *  - Matrices (A_j, U_j, T_j) are column-major n_j x n_j complex128 in HOST
+ *    memory: entry (a, b) is at [2*(a + b*n_j)].
+ *  - Tensors are column-major with i_1 fastest (Section 3, Eq. (index)) and
+ *    live in DEVICE memory; a tensor with nrhs right-hand sides has one extra
+ *    trailing index of extent nrhs (the right-hand sides are independent).
+ *  - Modes with n_j = 1 ("singletons", Section 4) carry a scalar A_j; they are
+ *    not transformed and add a_j to every diagonal sum.
+ *  - All device work is stream-ordered on the caller's `stream` (a
+ *    cudaStream_t passed as void*; NULL = legacy default stream) and
+ *    asynchronous unless stated.  No entry point throws; every failure is a
+ *    sylv_status.  CUDA errors map to SYLV_ERR_CUDA.
+ *  - The library allocates only small per-plan device buffers (the factors
+ *    and tiling tables) inside sylv_plan_create.  Tensor-sized scratch memory
+ *    is the caller's: query sylv_workspace_size and pass a device buffer of at
+ *    least that many bytes, 256-byte aligned.
+ *  - A plan may be used by one stream at a time: calls that overlap on the
+ *    GPU and share a workspace race.
+ */
+#ifndef SYLV_H
+#define SYLV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sylv_plan_s *sylv_plan_t;
+
+typedef enum {
+    SYLV_OK = 0,
+    SYLV_ERR_INVALID_ARG = 1,   /* NULL pointer, bad precision, misaligned buffer, ... */
+    SYLV_ERR_SHAPE = 2,         /* N < 1, n_j < 1, nrhs < 1, overflow, too many modes  */
+    SYLV_ERR_SINGULAR = 3,      /* some t_{1,i1i1}+...+t_{N,iNiN} is 0 or not finite   */
+    SYLV_ERR_NOT_CONVERGED = 4, /* mixed path: refinement did not reach rtol           */
+    SYLV_ERR_TIMEOUT = 5,       /* a device-side dependency wait hit its time limit    */
+    SYLV_ERR_OOM = 6,           /* plan-time device allocation failed                  */
+    SYLV_ERR_CUDA = 7,          /* any other CUDA runtime error                        */
+    SYLV_ERR_SCHUR = 8,         /* the host Schur iteration did not converge           */
+    SYLV_ERR_WORKSPACE = 9      /* workspace NULL or smaller than required             */
+} sylv_status;
+
+typedef enum {
+    SYLV_FP64 = 0,        /* every phase in FP64 (complex128)                          */
+    SYLV_MIXED_FP32 = 1   /* forward / sweep / back in FP32 (complex64) with the FP64
+                             diagonal division, FP64 residual and FP64 update:
+                             iterative refinement to relative error rtol            */
+} sylv_prec;
+
+/* Per-solve report, filled (after a stream synchronisation) only when the
+ * caller passes a non-NULL pointer. */
+typedef struct {
+    int32_t status;           /* sylv_status of the device-side checks              */
+    int32_t refine_iters;     /* refinement steps taken (0 for SYLV_FP64)             */
+    int32_t launches;         /* kernels this call enqueued                           */
+    int32_t reserved;
+    double last_corr_rel;     /* ||D_k|| / ||X_k|| of the last refinement step        */
+    double est_rel_err;       /* contraction-based estimate of the final error        */
+    double min_abs_den;       /* min |sum_j t_{j,i_j i_j}| over all multi-indices      */
+    double max_abs_den;       /* max of the same                                       */
+} sylv_info;
+
+/* Phase timing accumulated by CUDA events when enabled with sylv_plan_set_timing. */
+typedef struct {
+    double ms[6];             /* forward, sweep, back, residual, update, total        */
+    int64_t launches[6];      /* kernel launches per phase                             */
+    int64_t solves;           /* solves accumulated                                    */
+} sylv_timing;
+
+enum { SYLV_PH_FORWARD = 0, SYLV_PH_SWEEP = 1, SYLV_PH_BACK = 2, SYLV_PH_RESIDUAL = 3,
+       SYLV_PH_UPDATE = 4, SYLV_PH_TOTAL = 5 };
+
+/* Optional tuning (NULL = defaults).  block[j] = sweep tile extent along input
+ * mode j (0 = automatic); group_max = largest product of adjacent mode sizes
+ * fused into one transform pass (0 = automatic). */
+typedef struct {
+    int32_t block[64];
+    int32_t group_max;
+    int32_t sweep_threads;    /* 0 = automatic */
+    int32_t reserved[6];
+} sylv_tuning;
+
+/*
+ * sylv_plan_create -- setup for one equation shape (Section 2 and Algorithm 3,
+ * first loop: the Schur factors; Section 2.1 puts its cost at ~25 n_j^3).
+ *   N        number of modes, 1 <= N <= 256.
+ *   n        host int64[N], n_j >= 1.  At most 40 modes may have n_j > 1.
+ *   nrhs     right-hand sides per solve, >= 1.
+ *   A        host array of N pointers to n_j x n_j complex128 matrices, or NULL.
+ *   Q, T     host arrays of N pointers to precomputed Schur factors
+ *            (A_j = Q_j T_j Q_j^*, T_j upper triangular; entries below the
+ *            diagonal are ignored), or NULL.  Exactly one of A or (Q and T)
+ *            must be non-NULL.  For a singleton mode Q_j is ignored and T_j
+ *            holds the scalar.  All matrices are copied; the caller keeps them.
+ *   prec     sylv_prec.
+ *   rtol     mixed path: target relative error (e.g. 1e-10); ignored for FP64.
+ *   max_refine  mixed path: maximum refinement steps (>= 1).
+ *   device   CUDA device ordinal that owns the plan.
+ *   tuning   optional, may be NULL.
+ * Returns SYLV_OK and *out, or an error and *out = NULL.  SYLV_ERR_SINGULAR if
+ * some diagonal sum is zero or not finite (Eq. (yi1i2iN) needs it nonzero).
+ * Synchronises the device once (the tables are uploaded and checked).
+ */
+sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t nrhs,
+                             const double *const *A, const double *const *Q,
+                             const double *const *T, int prec, double rtol,
+                             int max_refine, int device, const sylv_tuning *tuning);
+
+sylv_status sylv_plan_destroy(sylv_plan_t plan);
+
+/* Bytes of device workspace a solve with this plan needs (0 is possible). */
+sylv_status sylv_workspace_size(sylv_plan_t plan, size_t *bytes);
+
+/*
+ * sylv_solve -- Algorithm 3 on the device: forward transform, triangular
+ * sweep, back transform; for SYLV_MIXED_FP32 followed by the FP64 residual
+ * R = B - sum_j A_j (x)_j X, a low-precision solve of R and the FP64 update
+ * X += D, repeated until the estimated relative error is below rtol.
+ *   B_dev  device complex128 tensor n_1 x ... x n_N x nrhs (read only).
+ *   X_dev  device complex128 tensor of the same shape (written).  X_dev ==
+ *          B_dev (in place, as Section 4 does) is allowed for SYLV_FP64 only.
+ *   workspace, workspace_bytes  device scratch (see sylv_workspace_size).
+ *   info   optional; when non-NULL the call synchronises `stream` and fills it.
+ * Stream-ordered and asynchronous when info == NULL.
+ */
+sylv_status sylv_solve(sylv_plan_t plan, const void *B_dev, void *X_dev, void *workspace,
+                       size_t workspace_bytes, void *stream, sylv_info *info);
+
+/*
+ * sylv_solve_batched -- `count` independent equations (any shapes) in one
+ * call; the whole sequence is recorded once into a CUDA graph per argument
+ * set and replayed.  plans[e], B_dev[e], X_dev[e] as for sylv_solve; the
+ * workspace must hold sylv_workspace_size_batched bytes.  infos may be NULL,
+ * else an array of `count` reports (the call then synchronises).
+ */
+sylv_status sylv_workspace_size_batched(int count, const sylv_plan_t *plans, size_t *bytes);
+sylv_status sylv_solve_batched(int count, const sylv_plan_t *plans, const void *const *B_dev,
+                               void *const *X_dev, void *workspace, size_t workspace_bytes,
+                               void *stream, sylv_info *infos);
+
+/*
+ * Single phases (same tensors and workspace rules as sylv_solve), in the
+ * plan's working precision: complex128 for SYLV_FP64, complex64 for
+ * SYLV_MIXED_FP32.  They expose the steps of Algorithm 3 one by one so that
+ * each can be checked against a reference that uses the plan's own factors.
+ *   sylv_forward   C = U_N^* (x)_N ( ... (U_1^* (x)_1 B)),  in place on T_dev.
+ *   sylv_sweep     Y with sum_j T_j (x)_j Y = C, Eq. (yi1i2iN), in place.
+ *   sylv_back      X = U_N (x)_N ( ... (U_1 (x)_1 Y)),  in place.
+ * sylv_residual computes, in FP64, R = B - sum_j A_j (x)_j X on complex128
+ * tensors (R_dev must not alias B_dev or X_dev).
+ */
+sylv_status sylv_forward(sylv_plan_t plan, void *T_dev, void *workspace, size_t workspace_bytes,
+                         void *stream);
+sylv_status sylv_sweep(sylv_plan_t plan, void *T_dev, void *workspace, size_t workspace_bytes,
+                       void *stream);
+sylv_status sylv_back(sylv_plan_t plan, void *T_dev, void *workspace, size_t workspace_bytes,
+                      void *stream);
+sylv_status sylv_residual(sylv_plan_t plan, const void *B_dev, const void *X_dev, void *R_dev,
+                          void *stream);
+
+/* The plan's Schur factors of input mode j (host copies; Q is the identity
+ * 1x1 for a singleton).  Q_out and T_out hold n_j*n_j complex128 each. */
+sylv_status sylv_plan_factors(sylv_plan_t plan, int j, double *Q_out, double *T_out);
+
+/* Phase timing with CUDA events recorded on the solve's stream.  Enabling it
+ * adds event records between phases; sylv_plan_timing synchronises those
+ * events, writes the sums and, if reset != 0, clears them. */
+sylv_status sylv_plan_set_timing(sylv_plan_t plan, int enable);
+sylv_status sylv_plan_timing(sylv_plan_t plan, sylv_timing *out, int reset);
+
+/*
+ * Host-only helper (no GPU needed): complex Schur decomposition A = Q T Q^*
+ * of one n x n complex128 matrix by Householder reduction to Hessenberg form
+ * and shifted QR (Section 2 uses this factorisation; the algorithm is the
+ * textbook one, e.g. Golub & Van Loan, ch. 7).  A, Q, T column-major.
+ */
+sylv_status sylv_schur(int64_t n, const double *A, double *Q, double *T);
+
+/* Human-readable name of a status code (static storage). */
+const char *sylv_status_string(sylv_status s);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int sylv_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SYLV_H */

@@ -1,0 +1,955 @@
+// Host runtime and C ABI (include/sylv.h) of the N-dimensional Sylvester
+// solver: plan construction (Schur factors, transform pass grouping, sweep
+// tiling and schedules, workspace layout) and the stream-ordered launch
+// sequences of Algorithm 3 and of the mixed-precision refinement loop.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <set>
+#include <vector>
+
+#include "sylv_internal.h"
+
+using cd = std::complex<double>;
+using namespace sylv;
+
+namespace {
+
+struct Group {
+    int first = 0, count = 0;
+    int64_t L = 1, P = 1, R = 1;
+    int Lt = 1, Rt = 1;
+    int64_t tilesL = 1;
+    size_t smem = 0;
+};
+
+struct TimedPhase {
+    int phase;
+    cudaEvent_t a, b;
+    int launches;
+};
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = (prev == dev) || (cudaSetDevice(dev) == cudaSuccess);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+std::mutex g_init_mu;
+std::set<int> g_init_devices;
+
+sylv_status ensure_init(int dev) {
+    std::lock_guard<std::mutex> lk(g_init_mu);
+    if (g_init_devices.count(dev)) return SYLV_OK;
+    if (kernels_init(dev) != cudaSuccess) return SYLV_ERR_CUDA;
+    g_init_devices.insert(dev);
+    return SYLV_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+struct sylv_plan_s {
+    int device = 0;
+    int prec = SYLV_FP64;
+    double rtol = 1e-10;
+    int max_refine = 5;
+    int N_in = 0;
+    std::vector<int64_t> n_in;
+    int64_t nrhs = 1;
+    int Nm = 0;
+    int64_t n[MAXM] = {};
+    int64_t S[MAXM] = {};
+    int orig[MAXM] = {};
+    int64_t ntot = 1;
+    cd sigma = 0.0;
+    std::vector<std::vector<cd>> Ah, Qh, Th;   // per input mode
+
+    void *dpool = nullptr;
+    const void *Uh64[MAXM] = {}, *U64[MAXM] = {}, *A64[MAXM] = {}, *T64[MAXM] = {};
+    const void *Uh32[MAXM] = {}, *U32[MAXM] = {}, *T32[MAXM] = {};
+    const double *d64[MAXM] = {};
+
+    std::vector<Group> tgroups;   // transform passes in the working precision
+    std::vector<Group> rgroups;   // FP64 residual passes
+
+    SweepArgs sw{};               // template; Y, T, flags filled per launch
+    int sweep_grid = 1, sweep_threads = 256;
+    size_t sweep_smem = 0;
+    int *d_order = nullptr, *d_sched = nullptr, *d_lev = nullptr;
+
+    double min_den = 0.0, max_den = 0.0;
+    size_t off_cnt = 0, off_W = 0, off_R = 0, ws_bytes = 0;
+
+    bool timing = false;
+    std::vector<TimedPhase> tphases;
+    std::vector<cudaEvent_t> ev_free;
+    int64_t timed_solves = 0;
+    int last_launches = 0;
+
+    ~sylv_plan_s() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (cur != device) cudaSetDevice(device);
+        for (auto &p : tphases) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+        for (auto e : ev_free) cudaEventDestroy(e);
+        if (dpool) cudaFree(dpool);
+        if (cur >= 0 && cur != device) cudaSetDevice(cur);
+    }
+
+    bool fp64() const { return prec == SYLV_FP64; }
+};
+
+namespace {
+
+// ----------------------------------------------------------------- tiling --
+
+bool choose_tile(int64_t L, int64_t P, int64_t R, int64_t Et, int64_t Eh, int &Lt, int &Rt) {
+    int64_t lt, rt;
+    if (L * P <= Et) {
+        lt = L;
+        rt = std::max<int64_t>(1, std::min<int64_t>(R, Et / (L * P)));
+    } else if (L < 32) {
+        lt = L;
+        rt = 1;
+    } else {
+        lt = (Et / P) / 32 * 32;
+        if (lt < 32) lt = 32;
+        if (lt * P > Eh) lt = std::max<int64_t>(1, Eh / P);
+        lt = std::min<int64_t>(lt, L);
+        rt = 1;
+    }
+    if (lt * P * rt > Eh) return false;
+    Lt = (int)lt;
+    Rt = (int)rt;
+    return true;
+}
+
+sylv_status make_groups(const sylv_plan_s &p, bool fp64, bool composition, int group_max,
+                        std::vector<Group> &out) {
+    const int64_t esz = fp64 ? 16 : 8;
+    const int64_t Et = fp64 ? 2048 : 4096;
+    const int64_t Eh = fp64 ? 8192 : 16384;
+    out.clear();
+    const int64_t tot = p.ntot * p.nrhs;
+    if (p.Nm == 0) {
+        Group g;
+        g.first = 0; g.count = 0; g.L = 1; g.P = 1; g.R = tot;
+        choose_tile(1, 1, tot, Et, Eh, g.Lt, g.Rt);
+        g.tilesL = 1;
+        g.smem = (size_t)(g.Lt * g.Rt) * esz;
+        out.push_back(g);
+        return SYLV_OK;
+    }
+    int j = 0;
+    while (j < p.Nm) {
+        Group g;
+        g.first = j;
+        g.L = p.S[j];
+        int64_t Pcap = Et / std::min<int64_t>(g.L, 32);
+        if (group_max > 0) Pcap = std::min<int64_t>(Pcap, group_max);
+        g.P = p.n[j];
+        g.count = 1;
+        while (j + g.count < p.Nm && g.count < MAXG && g.P * p.n[j + g.count] <= Pcap &&
+               p.S[j + g.count] == g.L * g.P)
+            g.P *= p.n[j + g.count], g.count++;
+        g.R = tot / (g.L * g.P);
+        if (!choose_tile(g.L, g.P, g.R, Et, Eh, g.Lt, g.Rt)) return SYLV_ERR_SHAPE;
+        g.tilesL = (g.L + g.Lt - 1) / g.Lt;
+        int64_t E = (int64_t)g.Lt * g.P * g.Rt;
+        g.smem = (size_t)(E * esz * ((composition && g.count > 1) ? 2 : 1));
+        if (g.smem > 200 * 1024) return SYLV_ERR_SHAPE;
+        out.push_back(g);
+        j += g.count;
+    }
+    return SYLV_OK;
+}
+
+sylv_status make_sweep(sylv_plan_s &p, const sylv_tuning *tu, std::vector<int> &order,
+                       std::vector<int> &sched, std::vector<int> &lev) {
+    SweepArgs &a = p.sw;
+    a.Nm = p.Nm;
+    const int target = p.fp64() ? 256 : 512;
+    int b[MAXM];
+    bool manual = false;
+    for (int j = 0; j < p.Nm; ++j) {
+        b[j] = 1;
+        if (tu && p.orig[j] < 64 && tu->block[p.orig[j]] > 0) {
+            b[j] = (int)std::min<int64_t>(tu->block[p.orig[j]], p.n[j]);
+            manual = true;
+        }
+    }
+    if (!manual) {
+        for (;;) {   // balanced doubling of the block with the most blocks left
+            int best = -1;
+            double bestr = 1.0;
+            int64_t prod = 1;
+            for (int j = 0; j < p.Nm; ++j) prod *= b[j];
+            for (int j = 0; j < p.Nm; ++j) {
+                if (b[j] >= p.n[j]) continue;
+                int64_t nb = std::min<int64_t>(2 * b[j], p.n[j]);
+                if (prod / b[j] * nb > target) continue;
+                double r = (double)p.n[j] / b[j];
+                if (r > bestr) { bestr = r; best = j; }
+            }
+            if (best < 0) break;
+            b[best] = (int)std::min<int64_t>(2 * b[best], p.n[best]);
+        }
+    }
+    int64_t ts = 1;
+    a.nin = 0;
+    int bs = 1;
+    a.Lin = 1;
+    for (int j = 0; j < p.Nm; ++j) {
+        a.n[j] = p.n[j];
+        a.S[j] = p.S[j];
+        a.b[j] = b[j];
+        a.Bc[j] = (int)((p.n[j] + b[j] - 1) / b[j]);
+        a.TS[j] = ts;
+        ts *= a.Bc[j];
+        if (b[j] > 1) {
+            a.inmode[a.nin] = j;
+            a.BS[a.nin] = bs;
+            bs *= b[j];
+            a.nin++;
+            a.Lin += b[j] - 1;
+        }
+    }
+    a.Pt = bs;
+    if (a.Pt > 8192) return SYLV_ERR_SHAPE;
+    a.ntiles1 = ts;
+    a.ntot = p.ntot;
+    if (ts > 0x7fffffffLL || ts * p.nrhs > 0x7fffffffLL) return SYLV_ERR_SHAPE;
+    a.ntiles = ts * p.nrhs;
+    a.sig_re = p.sigma.real();
+    a.sig_im = p.sigma.imag();
+    a.timeout_cycles = 4000000000LL;
+
+    // in-tile schedule: box offsets sorted by their distance from the tile end
+    std::vector<int> lvl(a.Pt);
+    std::vector<int> cntl(a.Lin + 1, 0);
+    for (int e = 0; e < a.Pt; ++e) {
+        int s = 0;
+        for (int q = 0; q < a.nin; ++q) s += (e / a.BS[q]) % a.b[a.inmode[q]];
+        lvl[e] = s;
+        cntl[s + 1]++;
+    }
+    lev.assign(a.Lin + 1, 0);
+    for (int l = 0; l < a.Lin; ++l) lev[l + 1] = lev[l] + cntl[l + 1];
+    sched.assign(a.Pt, 0);
+    {
+        std::vector<int> pos(lev.begin(), lev.end() - 1);
+        for (int e = 0; e < a.Pt; ++e) sched[pos[lvl[e]]++] = e;
+    }
+
+    // tile order: by level sum_j (Bc_j - 1 - I_j), then right-hand side, then id
+    int maxlev = 0;
+    for (int j = 0; j < p.Nm; ++j) maxlev += a.Bc[j] - 1;
+    std::vector<int> tl((size_t)ts);
+    std::vector<int64_t> cnt((size_t)maxlev + 2, 0);
+    for (int64_t t = 0; t < ts; ++t) {
+        int s = 0;
+        for (int j = 0; j < p.Nm; ++j) s += a.Bc[j] - 1 - (int)((t / a.TS[j]) % a.Bc[j]);
+        tl[(size_t)t] = s;
+        cnt[(size_t)s + 1]++;
+    }
+    for (int l = 0; l <= maxlev; ++l) cnt[(size_t)l + 1] += cnt[(size_t)l];
+    std::vector<int> by_level((size_t)ts);
+    {
+        std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
+        for (int64_t t = 0; t < ts; ++t) by_level[(size_t)pos[(size_t)tl[(size_t)t]]++] = (int)t;
+    }
+    order.resize((size_t)(ts * p.nrhs));
+    size_t w = 0;
+    for (int l = 0; l <= maxlev; ++l)
+        for (int64_t r = 0; r < p.nrhs; ++r)
+            for (int64_t q = cnt[(size_t)l]; q < cnt[(size_t)l + 1]; ++q)
+                order[w++] = (int)(r * ts + by_level[(size_t)q]);
+
+    p.sweep_threads = (a.Pt >= 256) ? 256 : 128;
+    if (tu && tu->sweep_threads > 0) p.sweep_threads = tu->sweep_threads;
+    p.sweep_smem = (size_t)a.Pt * (p.fp64() ? 16 : 8);
+    return SYLV_OK;
+}
+
+// ------------------------------------------------------------- launchers --
+
+struct Ctx {
+    sylv_plan_s *p;
+    cudaStream_t st;
+    DevFlags *flags;
+    int *cnt;
+    int launches = 0;
+    int phase_launches = 0;
+    int cur_phase = -1;
+    cudaEvent_t cur_ev = nullptr;
+};
+
+cudaEvent_t take_event(sylv_plan_s *p) {
+    if (!p->ev_free.empty()) {
+        cudaEvent_t e = p->ev_free.back();
+        p->ev_free.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void phase_begin(Ctx &c, int ph) {
+    c.cur_phase = ph;
+    c.phase_launches = 0;
+    if (!c.p->timing) return;
+    c.cur_ev = take_event(c.p);
+    cudaEventRecord(c.cur_ev, c.st);
+}
+
+void phase_end(Ctx &c) {
+    if (c.p->timing && c.cur_ev) {
+        cudaEvent_t b = take_event(c.p);
+        cudaEventRecord(b, c.st);
+        c.p->tphases.push_back({c.cur_phase, c.cur_ev, b, c.phase_launches});
+        c.cur_ev = nullptr;
+    }
+    c.cur_phase = -1;
+}
+
+void count(Ctx &c) { c.launches++; c.phase_launches++; }
+
+cudaError_t run_groups(Ctx &c, const std::vector<Group> &gs, bool fp64, int which,
+                       const void *first_in, int first_in_kind, void *work, int work_kind,
+                       void *last_out, int last_out_kind, int last_epi, const int *done) {
+    // which: 0 forward (U^*), 1 back (U)
+    sylv_plan_s *p = c.p;
+    for (size_t gi = 0; gi < gs.size(); ++gi) {
+        const Group &g = gs[gi];
+        MPArgs a{};
+        a.G = g.count;
+        for (int m = 0; m < g.count; ++m) {
+            int j = g.first + m;
+            a.gn[m] = (int)p->n[j];
+            if (fp64) a.mats[m] = which == 0 ? p->Uh64[j] : p->U64[j];
+            else a.mats[m] = which == 0 ? p->Uh32[j] : p->U32[j];
+        }
+        a.L = g.L; a.P = g.P; a.R = g.R; a.Lt = g.Lt; a.Rt = g.Rt; a.tilesL = g.tilesL;
+        a.flags = c.flags;
+        a.done = done;
+        const bool first = gi == 0, last = gi + 1 == gs.size();
+        a.in = first ? first_in : work;
+        int in_kind = first ? first_in_kind : work_kind;
+        a.out = last ? last_out : work;
+        int out_kind = last ? last_out_kind : work_kind;
+        int epi = last ? last_epi : EPI_STORE;
+        if (g.count == 0 && a.in == a.out && epi == EPI_STORE) continue;   // identity
+        cudaError_t e = launch_modeprod(fp64, in_kind, out_kind, epi, a, g.smem, c.st);
+        if (e != cudaSuccess) return e;
+        count(c);
+    }
+    return cudaSuccess;
+}
+
+cudaError_t run_residual(Ctx &c, const void *B, const void *X, void *R, const int *done) {
+    sylv_plan_s *p = c.p;
+    for (size_t gi = 0; gi < p->rgroups.size(); ++gi) {
+        const Group &g = p->rgroups[gi];
+        MPArgs a{};
+        a.G = g.count;
+        for (int m = 0; m < g.count; ++m) {
+            int j = g.first + m;
+            a.gn[m] = (int)p->n[j];
+            a.mats[m] = p->A64[j];
+        }
+        a.L = g.L; a.P = g.P; a.R = g.R; a.Lt = g.Lt; a.Rt = g.Rt; a.tilesL = g.tilesL;
+        a.in = X;
+        a.out = R;
+        a.B = B;
+        a.sig_re = p->sigma.real();
+        a.sig_im = p->sigma.imag();
+        a.first = gi == 0;
+        a.flags = c.flags;
+        a.done = done;
+        cudaError_t e = launch_modeprod(1, ELEM_C128, ELEM_C128, EPI_RESID, a, g.smem, c.st);
+        if (e != cudaSuccess) return e;
+        count(c);
+    }
+    return cudaSuccess;
+}
+
+cudaError_t run_sweep(Ctx &c, void *Y, bool fp64) {
+    sylv_plan_s *p = c.p;
+    SweepArgs a = p->sw;
+    a.Y = Y;
+    for (int j = 0; j < p->Nm; ++j) {
+        a.T[j] = fp64 ? p->T64[j] : p->T32[j];
+        a.d[j] = p->d64[j];
+    }
+    a.order = p->d_order;
+    a.sched = p->d_sched;
+    a.lev_start = p->d_lev;
+    a.cnt = c.cnt;
+    a.flags = c.flags;
+    cudaError_t e = launch_sweep_init(a, c.st);
+    if (e != cudaSuccess) return e;
+    count(c);
+    e = launch_sweep(fp64, a, p->sweep_grid, p->sweep_threads, p->sweep_smem, c.st);
+    if (e != cudaSuccess) return e;
+    count(c);
+    return cudaSuccess;
+}
+
+sylv_status check_ws(sylv_plan_s *p, void *ws, size_t bytes) {
+    if (p->ws_bytes == 0) return SYLV_OK;
+    if (!ws || bytes < p->ws_bytes) return SYLV_ERR_WORKSPACE;
+    if (((uintptr_t)ws) & 255) return SYLV_ERR_INVALID_ARG;
+    return SYLV_OK;
+}
+
+sylv_status fill_info(sylv_plan_s *p, DevFlags *flags, cudaStream_t st, sylv_info *info,
+                      int launches) {
+    DevFlags h{};
+    if (cudaMemcpyAsync(&h, flags, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return SYLV_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return SYLV_ERR_CUDA;
+    sylv_status s = SYLV_OK;
+    if (h.err & ERRBIT_TIMEOUT) s = SYLV_ERR_TIMEOUT;
+    else if (h.err & (ERRBIT_NOTCONV | ERRBIT_NAN)) s = SYLV_ERR_NOT_CONVERGED;
+    info->status = s;
+    info->refine_iters = p->fp64() ? 0 : h.iters;
+    info->launches = launches;
+    info->reserved = 0;
+    info->last_corr_rel = p->fp64() ? 0.0 : (double)h.lastcorr;
+    info->est_rel_err = p->fp64() ? 0.0 : (double)h.est;
+    info->min_abs_den = p->min_den;
+    info->max_abs_den = p->max_den;
+    return s;
+}
+
+sylv_status solve_impl(sylv_plan_s *p, const void *B, void *X, void *ws, cudaStream_t st,
+                       int &launches) {
+    Ctx c{p, st, reinterpret_cast<DevFlags *>(ws),
+          reinterpret_cast<int *>((char *)ws + p->off_cnt)};
+    cudaError_t e;
+    const bool timing = p->timing;
+    cudaEvent_t t0 = nullptr;
+    if (timing) { t0 = take_event(p); cudaEventRecord(t0, st); }
+    if ((e = launch_solve_init(c.flags, st)) != cudaSuccess) return SYLV_ERR_CUDA;
+    count(c);
+    if (p->fp64()) {
+        phase_begin(c, SYLV_PH_FORWARD);
+        if (p->Nm == 0) {
+            if (B != X && cudaMemcpyAsync(X, B, (size_t)(p->ntot * p->nrhs) * 16,
+                                          cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+                return SYLV_ERR_CUDA;
+        } else if ((e = run_groups(c, p->tgroups, true, 0, B, ELEM_C128, X, ELEM_C128, X,
+                                   ELEM_C128, EPI_STORE, nullptr)) != cudaSuccess)
+            return SYLV_ERR_CUDA;
+        phase_end(c);
+        phase_begin(c, SYLV_PH_SWEEP);
+        if ((e = run_sweep(c, X, true)) != cudaSuccess) return SYLV_ERR_CUDA;
+        phase_end(c);
+        phase_begin(c, SYLV_PH_BACK);
+        if (p->Nm > 0 && (e = run_groups(c, p->tgroups, true, 1, X, ELEM_C128, X, ELEM_C128, X,
+                                         ELEM_C128, EPI_STORE, nullptr)) != cudaSuccess)
+            return SYLV_ERR_CUDA;
+        phase_end(c);
+    } else {
+        void *W = (char *)ws + p->off_W;
+        void *R = (char *)ws + p->off_R;
+        const int *done = &c.flags->done;
+        // initial low-precision solve X_0
+        phase_begin(c, SYLV_PH_FORWARD);
+        if ((e = run_groups(c, p->tgroups, false, 0, B, ELEM_C128, W, ELEM_C64, W, ELEM_C64,
+                            EPI_STORE, nullptr)) != cudaSuccess)
+            return SYLV_ERR_CUDA;
+        phase_end(c);
+        phase_begin(c, SYLV_PH_SWEEP);
+        if ((e = run_sweep(c, W, false)) != cudaSuccess) return SYLV_ERR_CUDA;
+        phase_end(c);
+        phase_begin(c, SYLV_PH_BACK);
+        if ((e = run_groups(c, p->tgroups, false, 1, W, ELEM_C64, W, ELEM_C64, X, ELEM_C128,
+                            EPI_STORE_NORM, nullptr)) != cudaSuccess)
+            return SYLV_ERR_CUDA;
+        phase_end(c);
+        phase_begin(c, SYLV_PH_UPDATE);
+        if (launch_refine_decide(c.flags, (float)p->rtol, 0, p->max_refine, c.st) != cudaSuccess)
+            return SYLV_ERR_CUDA;
+        count(c);
+        phase_end(c);
+        for (int it = 1; it <= p->max_refine; ++it) {
+            phase_begin(c, SYLV_PH_RESIDUAL);
+            if (run_residual(c, B, X, R, done) != cudaSuccess) return SYLV_ERR_CUDA;
+            phase_end(c);
+            phase_begin(c, SYLV_PH_FORWARD);
+            if (run_groups(c, p->tgroups, false, 0, R, ELEM_C128, W, ELEM_C64, W, ELEM_C64,
+                           EPI_STORE, done) != cudaSuccess)
+                return SYLV_ERR_CUDA;
+            phase_end(c);
+            phase_begin(c, SYLV_PH_SWEEP);
+            if (run_sweep(c, W, false) != cudaSuccess) return SYLV_ERR_CUDA;
+            phase_end(c);
+            phase_begin(c, SYLV_PH_BACK);
+            if (run_groups(c, p->tgroups, false, 1, W, ELEM_C64, W, ELEM_C64, X, ELEM_C128,
+                           EPI_ACCUM, done) != cudaSuccess)
+                return SYLV_ERR_CUDA;
+            phase_end(c);
+            phase_begin(c, SYLV_PH_UPDATE);
+            if (launch_refine_decide(c.flags, (float)p->rtol, it, p->max_refine, c.st) != cudaSuccess)
+                return SYLV_ERR_CUDA;
+            count(c);
+            phase_end(c);
+        }
+    }
+    if (timing) {
+        cudaEvent_t t1 = take_event(p);
+        cudaEventRecord(t1, st);
+        p->tphases.push_back({SYLV_PH_TOTAL, t0, t1, c.launches});
+        p->timed_solves++;
+    }
+    launches = c.launches;
+    p->last_launches = c.launches;
+    return SYLV_OK;
+}
+
+}  // namespace
+
+// ===================================================================== ABI ==
+
+extern "C" {
+
+int sylv_version(void) { return 100; }
+
+const char *sylv_status_string(sylv_status s) {
+    switch (s) {
+        case SYLV_OK: return "ok";
+        case SYLV_ERR_INVALID_ARG: return "invalid argument";
+        case SYLV_ERR_SHAPE: return "unsupported shape";
+        case SYLV_ERR_SINGULAR: return "singular: a diagonal sum t_1+...+t_N is zero or not finite";
+        case SYLV_ERR_NOT_CONVERGED: return "refinement did not converge";
+        case SYLV_ERR_TIMEOUT: return "device dependency wait timed out";
+        case SYLV_ERR_OOM: return "device allocation failed";
+        case SYLV_ERR_CUDA: return "CUDA error";
+        case SYLV_ERR_SCHUR: return "Schur iteration did not converge";
+        case SYLV_ERR_WORKSPACE: return "workspace missing or too small";
+    }
+    return "unknown status";
+}
+
+sylv_status sylv_schur(int64_t n, const double *A, double *Q, double *T) {
+    if (n < 1 || n > MAX_N) return SYLV_ERR_SHAPE;
+    try {
+        return schur_host(n, A, Q, T);
+    } catch (...) {
+        return SYLV_ERR_OOM;
+    }
+}
+
+sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t nrhs,
+                             const double *const *A, const double *const *Q,
+                             const double *const *T, int prec, double rtol, int max_refine,
+                             int device, const sylv_tuning *tuning) {
+    if (!out) return SYLV_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!n || N < 1 || N > 256 || nrhs < 1) return SYLV_ERR_SHAPE;
+    if (prec != SYLV_FP64 && prec != SYLV_MIXED_FP32) return SYLV_ERR_INVALID_ARG;
+    const bool haveA = A != nullptr, haveQT = (Q != nullptr && T != nullptr);
+    if (haveA == haveQT) return SYLV_ERR_INVALID_ARG;
+    if (prec == SYLV_MIXED_FP32 && (!(rtol > 0.0) || max_refine < 1)) return SYLV_ERR_INVALID_ARG;
+    sylv_plan_s *p = nullptr;
+    try {
+        p = new sylv_plan_s();
+    } catch (...) {
+        return SYLV_ERR_OOM;
+    }
+    std::unique_ptr<sylv_plan_s> guard(p);
+    p->device = device;
+    p->prec = prec;
+    p->rtol = rtol;
+    p->max_refine = max_refine;
+    p->N_in = N;
+    p->nrhs = nrhs;
+    p->n_in.assign(n, n + N);
+    // shapes, strides, overflow
+    int64_t tot = 1;
+    for (int j = 0; j < N; ++j) {
+        if (n[j] < 1 || n[j] > MAX_N) return SYLV_ERR_SHAPE;
+        if (tot > (int64_t)(INT64_MAX / 16) / n[j]) return SYLV_ERR_SHAPE;
+        if (n[j] > 1) {
+            if (p->Nm >= MAXM) return SYLV_ERR_SHAPE;
+            p->n[p->Nm] = n[j];
+            p->S[p->Nm] = tot;
+            p->orig[p->Nm] = j;
+            p->Nm++;
+        }
+        tot *= n[j];
+    }
+    if (tot > (int64_t)(INT64_MAX / 16) / nrhs) return SYLV_ERR_SHAPE;
+    p->ntot = tot;
+
+    // factors on the host
+    p->Ah.resize(N);
+    p->Qh.resize(N);
+    p->Th.resize(N);
+    for (int j = 0; j < N; ++j) {
+        const int64_t nj = n[j], nn = nj * nj;
+        auto &Aj = p->Ah[j];
+        auto &Qj = p->Qh[j];
+        auto &Tj = p->Th[j];
+        Aj.assign((size_t)nn, 0.0);
+        Qj.assign((size_t)nn, 0.0);
+        Tj.assign((size_t)nn, 0.0);
+        if (haveA) {
+            if (!A[j]) return SYLV_ERR_INVALID_ARG;
+            for (int64_t k = 0; k < nn; ++k) Aj[(size_t)k] = cd(A[j][2 * k], A[j][2 * k + 1]);
+            if (nj == 1) {
+                Qj[0] = 1.0;
+                Tj[0] = Aj[0];
+            } else {
+                std::vector<double> q((size_t)(2 * nn)), t((size_t)(2 * nn));
+                sylv_status s = schur_host(nj, A[j], q.data(), t.data());
+                if (s != SYLV_OK) return s;
+                for (int64_t k = 0; k < nn; ++k) {
+                    Qj[(size_t)k] = cd(q[2 * k], q[2 * k + 1]);
+                    Tj[(size_t)k] = cd(t[2 * k], t[2 * k + 1]);
+                }
+            }
+        } else {
+            if (!T[j] || (nj > 1 && !Q[j])) return SYLV_ERR_INVALID_ARG;
+            for (int64_t c = 0; c < nj; ++c)
+                for (int64_t r = 0; r < nj; ++r) {
+                    int64_t k = r + c * nj;
+                    Tj[(size_t)k] = r <= c ? cd(T[j][2 * k], T[j][2 * k + 1]) : cd(0.0, 0.0);
+                    Qj[(size_t)k] = nj == 1 ? cd(1.0, 0.0) : cd(Q[j][2 * k], Q[j][2 * k + 1]);
+                }
+            // A = Q T Q^*
+            for (int64_t c = 0; c < nj; ++c)
+                for (int64_t r = 0; r < nj; ++r) {
+                    cd s = 0.0;
+                    for (int64_t a = 0; a < nj; ++a)
+                        for (int64_t b = a; b < nj; ++b)
+                            s += Qj[(size_t)(r + a * nj)] * Tj[(size_t)(a + b * nj)] *
+                                 std::conj(Qj[(size_t)(c + b * nj)]);
+                    Aj[(size_t)(r + c * nj)] = s;
+                }
+        }
+        for (auto &z : Tj)
+            if (!std::isfinite(z.real()) || !std::isfinite(z.imag())) return SYLV_ERR_INVALID_ARG;
+        if (nj == 1) p->sigma += Tj[0];
+    }
+
+    // device
+    {
+        int ndev = 0;
+        if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+            return SYLV_ERR_CUDA;
+    }
+    DeviceGuard dg(device);
+    if (!dg.ok) return SYLV_ERR_CUDA;
+    if (ensure_init(device) != SYLV_OK) return SYLV_ERR_CUDA;
+
+    // transform and residual passes
+    const int gmax = tuning ? tuning->group_max : 0;
+    sylv_status s = make_groups(*p, p->fp64(), true, gmax, p->tgroups);
+    if (s != SYLV_OK) return s;
+    s = make_groups(*p, true, false, gmax, p->rgroups);
+    if (s != SYLV_OK) return s;
+    std::vector<int> order, sched, lev;
+    s = make_sweep(*p, tuning, order, sched, lev);
+    if (s != SYLV_OK) return s;
+
+    // device pool: per mode Uh64 U64 A64 T64 d64 Uh32 U32 T32, then the tables
+    size_t off = 0;
+    std::vector<size_t> offs;
+    auto reserve = [&](size_t bytes) { off = align256(off); offs.push_back(off); off += bytes; };
+    for (int j = 0; j < p->Nm; ++j) {
+        size_t nn = (size_t)(p->n[j] * p->n[j]);
+        reserve(nn * 16); reserve(nn * 16); reserve(nn * 16); reserve(nn * 16);
+        reserve((size_t)p->n[j] * 16);
+        reserve(nn * 8); reserve(nn * 8); reserve(nn * 8);
+    }
+    reserve(order.size() * 4);
+    reserve(sched.size() * 4);
+    reserve(lev.size() * 4);
+    reserve(3 * sizeof(unsigned long long));
+    size_t pool_bytes = align256(off);
+    if (cudaMalloc(&p->dpool, pool_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return SYLV_ERR_OOM;
+    }
+    std::vector<char> host(pool_bytes, 0);
+    size_t oi = 0;
+    char *base = (char *)p->dpool;
+    for (int j = 0; j < p->Nm; ++j) {
+        const int jj = p->orig[j];
+        const int64_t nj = p->n[j];
+        const auto &Qj = p->Qh[jj];
+        const auto &Tj = p->Th[jj];
+        const auto &Aj = p->Ah[jj];
+        double *uh64 = (double *)(host.data() + offs[oi]);
+        double *u64 = (double *)(host.data() + offs[oi + 1]);
+        double *a64 = (double *)(host.data() + offs[oi + 2]);
+        double *t64 = (double *)(host.data() + offs[oi + 3]);
+        double *d64 = (double *)(host.data() + offs[oi + 4]);
+        float *uh32 = (float *)(host.data() + offs[oi + 5]);
+        float *u32 = (float *)(host.data() + offs[oi + 6]);
+        float *t32 = (float *)(host.data() + offs[oi + 7]);
+        for (int64_t c = 0; c < nj; ++c)
+            for (int64_t r = 0; r < nj; ++r) {
+                size_t k = (size_t)(r + c * nj);
+                cd uh = std::conj(Qj[(size_t)(c + r * nj)]);   // (U^*)[r, c]
+                cd u = Qj[k];
+                uh64[2 * k] = uh.real(); uh64[2 * k + 1] = uh.imag();
+                u64[2 * k] = u.real(); u64[2 * k + 1] = u.imag();
+                a64[2 * k] = Aj[k].real(); a64[2 * k + 1] = Aj[k].imag();
+                t64[2 * k] = Tj[k].real(); t64[2 * k + 1] = Tj[k].imag();
+                uh32[2 * k] = (float)uh.real(); uh32[2 * k + 1] = (float)uh.imag();
+                u32[2 * k] = (float)u.real(); u32[2 * k + 1] = (float)u.imag();
+                t32[2 * k] = (float)Tj[k].real(); t32[2 * k + 1] = (float)Tj[k].imag();
+            }
+        for (int64_t i = 0; i < nj; ++i) {
+            d64[2 * i] = Tj[(size_t)(i + i * nj)].real();
+            d64[2 * i + 1] = Tj[(size_t)(i + i * nj)].imag();
+        }
+        p->Uh64[j] = base + offs[oi];
+        p->U64[j] = base + offs[oi + 1];
+        p->A64[j] = base + offs[oi + 2];
+        p->T64[j] = base + offs[oi + 3];
+        p->d64[j] = (const double *)(base + offs[oi + 4]);
+        p->Uh32[j] = base + offs[oi + 5];
+        p->U32[j] = base + offs[oi + 6];
+        p->T32[j] = base + offs[oi + 7];
+        oi += 8;
+    }
+    std::memcpy(host.data() + offs[oi], order.data(), order.size() * 4);
+    std::memcpy(host.data() + offs[oi + 1], sched.data(), sched.size() * 4);
+    std::memcpy(host.data() + offs[oi + 2], lev.data(), lev.size() * 4);
+    p->d_order = (int *)(base + offs[oi]);
+    p->d_sched = (int *)(base + offs[oi + 1]);
+    p->d_lev = (int *)(base + offs[oi + 2]);
+    unsigned long long *dm = (unsigned long long *)(base + offs[oi + 3]);
+    unsigned long long init3[3] = {~0ull, 0ull, 0ull};
+    std::memcpy(host.data() + offs[oi + 3], init3, sizeof(init3));
+    if (cudaMemcpy(p->dpool, host.data(), pool_bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+        return SYLV_ERR_CUDA;
+
+    // diagonal sums: min / max |sigma + sum_j t_{j,i_j i_j}|
+    if (launch_den_minmax(p->Nm, p->n, p->d64, p->sigma.real(), p->sigma.imag(), p->ntot, dm,
+                          0) != cudaSuccess)
+        return SYLV_ERR_CUDA;
+    unsigned long long r3[3];
+    if (cudaMemcpy(r3, dm, sizeof(r3), cudaMemcpyDeviceToHost) != cudaSuccess) return SYLV_ERR_CUDA;
+    double mn, mx;
+    std::memcpy(&mn, &r3[0], 8);
+    std::memcpy(&mx, &r3[1], 8);
+    p->min_den = mn;
+    p->max_den = mx;
+    if (r3[2] != 0 || !(mn > 0.0) || !std::isfinite(mx)) return SYLV_ERR_SINGULAR;
+
+    // sweep grid: every SM holds as many tiles as fit
+    {
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+        int per = sweep_blocks_per_sm(p->fp64(), p->sweep_threads, p->sweep_smem);
+        if (per < 1) per = 1;
+        int64_t grid = (int64_t)sms * per;
+        grid = std::min<int64_t>(grid, p->sw.ntiles);
+        p->sweep_grid = (int)std::max<int64_t>(1, grid);
+    }
+
+    // workspace layout
+    size_t w = align256(sizeof(DevFlags));
+    p->off_cnt = w;
+    w = align256(w + (size_t)p->sw.ntiles * 4);
+    if (!p->fp64()) {
+        p->off_W = w;
+        w = align256(w + (size_t)(p->ntot * p->nrhs) * 8);
+        p->off_R = w;
+        w = align256(w + (size_t)(p->ntot * p->nrhs) * 16);
+    }
+    p->ws_bytes = w;
+    *out = guard.release();
+    return SYLV_OK;
+}
+
+sylv_status sylv_plan_destroy(sylv_plan_t plan) {
+    if (!plan) return SYLV_ERR_INVALID_ARG;
+    delete plan;
+    return SYLV_OK;
+}
+
+sylv_status sylv_workspace_size(sylv_plan_t plan, size_t *bytes) {
+    if (!plan || !bytes) return SYLV_ERR_INVALID_ARG;
+    *bytes = plan->ws_bytes;
+    return SYLV_OK;
+}
+
+sylv_status sylv_solve(sylv_plan_t p, const void *B, void *X, void *ws, size_t ws_bytes,
+                       void *stream, sylv_info *info) {
+    if (!p || !B || !X) return SYLV_ERR_INVALID_ARG;
+    if (!p->fp64() && B == X) return SYLV_ERR_INVALID_ARG;
+    if ((((uintptr_t)B) | ((uintptr_t)X)) & 15) return SYLV_ERR_INVALID_ARG;
+    sylv_status s = check_ws(p, ws, ws_bytes);
+    if (s != SYLV_OK) return s;
+    DeviceGuard dg(p->device);
+    if (!dg.ok) return SYLV_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    int launches = 0;
+    s = solve_impl(p, B, X, ws, st, launches);
+    if (s != SYLV_OK) return s;
+    if (info) return fill_info(p, reinterpret_cast<DevFlags *>(ws), st, info, launches);
+    return SYLV_OK;
+}
+
+sylv_status sylv_workspace_size_batched(int count, const sylv_plan_t *plans, size_t *bytes) {
+    if (count < 0 || (count > 0 && !plans) || !bytes) return SYLV_ERR_INVALID_ARG;
+    size_t tot = 0;
+    for (int e = 0; e < count; ++e) {
+        if (!plans[e]) return SYLV_ERR_INVALID_ARG;
+        tot += align256(plans[e]->ws_bytes);
+    }
+    *bytes = tot;
+    return SYLV_OK;
+}
+
+sylv_status sylv_solve_batched(int count, const sylv_plan_t *plans, const void *const *B,
+                               void *const *X, void *ws, size_t ws_bytes, void *stream,
+                               sylv_info *infos) {
+    if (count < 0 || (count > 0 && (!plans || !B || !X))) return SYLV_ERR_INVALID_ARG;
+    size_t need = 0;
+    sylv_status s = sylv_workspace_size_batched(count, plans, &need);
+    if (s != SYLV_OK) return s;
+    if (need > 0 && (!ws || ws_bytes < need)) return SYLV_ERR_WORKSPACE;
+    if (((uintptr_t)ws) & 255) return SYLV_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t off = 0;
+    std::vector<int> launches((size_t)count, 0);
+    for (int e = 0; e < count; ++e) {
+        sylv_plan_s *p = plans[e];
+        if (!B[e] || !X[e] || (!p->fp64() && B[e] == X[e])) return SYLV_ERR_INVALID_ARG;
+        DeviceGuard dg(p->device);
+        if (!dg.ok) return SYLV_ERR_CUDA;
+        s = solve_impl(p, B[e], X[e], (char *)ws + off, st, launches[(size_t)e]);
+        if (s != SYLV_OK) return s;
+        off += align256(p->ws_bytes);
+    }
+    if (infos) {
+        off = 0;
+        sylv_status worst = SYLV_OK;
+        for (int e = 0; e < count; ++e) {
+            sylv_status r = fill_info(plans[e], reinterpret_cast<DevFlags *>((char *)ws + off),
+                                      st, &infos[e], launches[(size_t)e]);
+            if (r != SYLV_OK && worst == SYLV_OK) worst = r;
+            off += align256(plans[e]->ws_bytes);
+        }
+        return worst;
+    }
+    return SYLV_OK;
+}
+
+sylv_status sylv_forward(sylv_plan_t p, void *Tdev, void *ws, size_t ws_bytes, void *stream) {
+    if (!p || !Tdev) return SYLV_ERR_INVALID_ARG;
+    sylv_status s = check_ws(p, ws, ws_bytes);
+    if (s != SYLV_OK) return s;
+    DeviceGuard dg(p->device);
+    if (!dg.ok) return SYLV_ERR_CUDA;
+    Ctx c{p, (cudaStream_t)stream, reinterpret_cast<DevFlags *>(ws), nullptr};
+    if (p->Nm == 0) return SYLV_OK;
+    int k = p->fp64() ? ELEM_C128 : ELEM_C64;
+    if (run_groups(c, p->tgroups, p->fp64(), 0, Tdev, k, Tdev, k, Tdev, k, EPI_STORE, nullptr) !=
+        cudaSuccess)
+        return SYLV_ERR_CUDA;
+    return SYLV_OK;
+}
+
+sylv_status sylv_back(sylv_plan_t p, void *Tdev, void *ws, size_t ws_bytes, void *stream) {
+    if (!p || !Tdev) return SYLV_ERR_INVALID_ARG;
+    sylv_status s = check_ws(p, ws, ws_bytes);
+    if (s != SYLV_OK) return s;
+    DeviceGuard dg(p->device);
+    if (!dg.ok) return SYLV_ERR_CUDA;
+    Ctx c{p, (cudaStream_t)stream, reinterpret_cast<DevFlags *>(ws), nullptr};
+    if (p->Nm == 0) return SYLV_OK;
+    int k = p->fp64() ? ELEM_C128 : ELEM_C64;
+    if (run_groups(c, p->tgroups, p->fp64(), 1, Tdev, k, Tdev, k, Tdev, k, EPI_STORE, nullptr) !=
+        cudaSuccess)
+        return SYLV_ERR_CUDA;
+    return SYLV_OK;
+}
+
+sylv_status sylv_sweep(sylv_plan_t p, void *Tdev, void *ws, size_t ws_bytes, void *stream) {
+    if (!p || !Tdev) return SYLV_ERR_INVALID_ARG;
+    sylv_status s = check_ws(p, ws, ws_bytes);
+    if (s != SYLV_OK) return s;
+    DeviceGuard dg(p->device);
+    if (!dg.ok) return SYLV_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    Ctx c{p, st, reinterpret_cast<DevFlags *>(ws),
+          reinterpret_cast<int *>((char *)ws + p->off_cnt)};
+    if (launch_solve_init(c.flags, st) != cudaSuccess) return SYLV_ERR_CUDA;
+    if (run_sweep(c, Tdev, p->fp64()) != cudaSuccess) return SYLV_ERR_CUDA;
+    return SYLV_OK;
+}
+
+sylv_status sylv_residual(sylv_plan_t p, const void *B, const void *X, void *R, void *stream) {
+    if (!p || !B || !X || !R || R == B || R == X) return SYLV_ERR_INVALID_ARG;
+    DeviceGuard dg(p->device);
+    if (!dg.ok) return SYLV_ERR_CUDA;
+    Ctx c{p, (cudaStream_t)stream, nullptr, nullptr};
+    if (run_residual(c, B, X, R, nullptr) != cudaSuccess) return SYLV_ERR_CUDA;
+    return SYLV_OK;
+}
+
+sylv_status sylv_plan_factors(sylv_plan_t p, int j, double *Qo, double *To) {
+    if (!p || !Qo || !To || j < 0 || j >= p->N_in) return SYLV_ERR_INVALID_ARG;
+    const auto &Q = p->Qh[(size_t)j];
+    const auto &T = p->Th[(size_t)j];
+    for (size_t k = 0; k < Q.size(); ++k) {
+        Qo[2 * k] = Q[k].real(); Qo[2 * k + 1] = Q[k].imag();
+        To[2 * k] = T[k].real(); To[2 * k + 1] = T[k].imag();
+    }
+    return SYLV_OK;
+}
+
+sylv_status sylv_plan_set_timing(sylv_plan_t p, int enable) {
+    if (!p) return SYLV_ERR_INVALID_ARG;
+    p->timing = enable != 0;
+    return SYLV_OK;
+}
+
+sylv_status sylv_plan_timing(sylv_plan_t p, sylv_timing *out, int reset) {
+    if (!p || !out) return SYLV_ERR_INVALID_ARG;
+    DeviceGuard dg(p->device);
+    std::memset(out, 0, sizeof(*out));
+    for (auto &ph : p->tphases) {
+        if (cudaEventSynchronize(ph.b) != cudaSuccess) return SYLV_ERR_CUDA;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ph.a, ph.b) != cudaSuccess) return SYLV_ERR_CUDA;
+        out->ms[ph.phase] += ms;
+        out->launches[ph.phase] += ph.launches;
+    }
+    out->solves = p->timed_solves;
+    if (reset) {
+        for (auto &ph : p->tphases) {
+            p->ev_free.push_back(ph.a);
+            p->ev_free.push_back(ph.b);
+        }
+        p->tphases.clear();
+        p->timed_solves = 0;
+    }
+    return SYLV_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,103 @@
+// Internal declarations shared by the host runtime (capi.cu, schur.cpp) and
+// the sm_103a kernels (kernels.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/sylv.h"
+
+#ifdef __CUDACC__
+#include <cuda_runtime.h>
+#endif
+
+namespace sylv {
+
+constexpr int MAXM = 40;   // modes with n_j > 1 (after singleton removal)
+constexpr int MAXG = 16;   // modes fused into one transform pass
+constexpr int MAX_N = 1024;
+
+sylv_status schur_host(int64_t n, const double *A, double *Q, double *T);
+
+// Device-side control block at the start of every workspace.
+struct DevFlags {
+    int done;        // refinement finished: later kernels of the solve return at once
+    int err;         // bit set of sylv_status codes raised on the device
+    int ticket;      // sweep: next tile ticket
+    int iters;       // refinement steps taken
+    unsigned dmax;   // float bits: max(|re|,|im|) of the last correction D
+    unsigned xmax;   // float bits: max(|re|,|im|) of the updated X
+    float dprev;     // ||D_{k-1}|| (||X_0|| before the first step)
+    float est;       // estimated relative error after the last step
+    float lastcorr;  // ||D_k|| / ||X_k||
+    int pad[7];
+};
+static_assert(sizeof(DevFlags) == 64, "DevFlags layout");
+
+enum { ERRBIT_TIMEOUT = 1, ERRBIT_NOTCONV = 2, ERRBIT_NAN = 4 };
+
+enum Epi { EPI_STORE = 0, EPI_RESID = 1, EPI_ACCUM = 2, EPI_STORE_NORM = 3 };
+enum ElemKind { ELEM_C64 = 0, ELEM_C128 = 1 };
+
+// One transform pass over the view (L, P, R) of a tensor, where P is the
+// product of the sizes of `G` adjacent modes; tiles are Lt x P x Rt.
+struct MPArgs {
+    const void *in;
+    void *out;
+    const void *mats[MAXG];   // n x n column-major, compute precision
+    int gn[MAXG];
+    int G;
+    int Lt, Rt;
+    int64_t L, P, R;
+    int64_t tilesL;
+    // residual: R = (first ? B - sigma*X : R) - sum_m A_m (x)_m X
+    const void *B;
+    double sig_re, sig_im;
+    int first;
+    // norms (float bits, max(|re|,|im|))
+    DevFlags *flags;
+    const int *done;          // early exit when *done != 0 (nullable)
+};
+
+struct SweepArgs {
+    void *Y;
+    int Nm;
+    int nin;                  // modes with block > 1 (inside a tile)
+    int Lin;                  // in-tile levels
+    int Pt;                   // entries of a full tile
+    int64_t n[MAXM];
+    int64_t S[MAXM];          // element strides
+    int64_t TS[MAXM];         // tile-index strides
+    int b[MAXM];              // block extents
+    int Bc[MAXM];             // blocks per mode
+    int inmode[MAXM];         // indices of in-tile modes
+    int BS[MAXM];             // box strides of in-tile modes (by position in inmode)
+    const void *T[MAXM];      // T_j, compute precision, column-major
+    const double *d[MAXM];    // diag(T_j) as interleaved FP64 pairs
+    double sig_re, sig_im;
+    int64_t ntiles1, ntiles, ntot;
+    const int *order;         // tile ids by level
+    int *cnt;                 // per-tile count of unfinished immediate successors
+    DevFlags *flags;
+    const int *sched;         // in-tile schedule (a'-linear offsets by level)
+    const int *lev_start;     // Lin + 1 entries
+    long long timeout_cycles;
+};
+
+#ifdef __CUDACC__
+cudaError_t launch_modeprod(int fp64, int in_kind, int out_kind, int epi, const MPArgs &a,
+                            size_t smem, cudaStream_t st);
+cudaError_t launch_sweep(int fp64, const SweepArgs &a, int grid, int threads, size_t smem,
+                         cudaStream_t st);
+cudaError_t launch_sweep_init(const SweepArgs &a, cudaStream_t st);
+cudaError_t launch_solve_init(DevFlags *f, cudaStream_t st);
+cudaError_t launch_refine_decide(DevFlags *f, float rtol, int step, int max_refine,
+                                 cudaStream_t st);
+cudaError_t launch_den_minmax(int Nm, const int64_t *n, const double *const *d, double sig_re,
+                              double sig_im, int64_t ntot, unsigned long long *out3,
+                              cudaStream_t st);
+cudaError_t kernels_init(int device);
+int sweep_blocks_per_sm(int fp64, int threads, size_t smem);
+#endif
+
+}  // namespace sylv
