@@ -176,6 +176,33 @@ sylv_status sylv_back(sylv_plan_t plan, void *T_dev, void *workspace, size_t wor
 sylv_status sylv_residual(sylv_plan_t plan, const void *B_dev, const void *X_dev, void *R_dev,
                           void *stream);
 
+/*
+ * sylv_sweep_static -- the same triangular sweep as sylv_sweep, for callers
+ * that cannot allocate device memory at all: code that runs with a fixed
+ * device-memory budget fully reserved up front (for instance by another
+ * framework's caching allocator, so a cudaMalloc would fail), or code in a
+ * latency-critical loop where a cudaMalloc/cudaFree would stall on an
+ * implicit device synchronisation.  The paper has no counterpart; this is a
+ * service of this library.
+ *
+ * The sweep's scratch (a 64-byte control block plus one int per tile) comes
+ * from one array of SYLV_STATIC_SCRATCH_BYTES inside the library, which every
+ * GPU that loads the library holds until the process exits; nothing is
+ * allocated and no workspace is passed.  T_dev is as for sylv_sweep (plan's
+ * working precision, in place).
+ *  - Plans whose sweep needs more than SYLV_STATIC_SCRATCH_BYTES
+ *    (64 + 4 * tiles, rounded up to 256) are rejected with SYLV_ERR_SHAPE.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - Every call on a device shares the one array and leaves its contents
+ *    behind; each call clears what must start at zero before it sweeps.
+ *    Calls whose work overlaps on the GPU (other streams, other threads,
+ *    other plans) race on the array and give wrong results: serialise them.
+ */
+#define SYLV_STATIC_SCRATCH_BYTES (1u << 20)
+sylv_status sylv_sweep_static(sylv_plan_t plan, void *T_dev, void *stream);
+
 /* The plan's Schur factors of input mode j (host copies; Q is the identity
  * 1x1 for a singleton).  Q_out and T_out hold n_j*n_j complex128 each. */
 sylv_status sylv_plan_factors(sylv_plan_t plan, int j, double *Q_out, double *T_out);

@@ -31,7 +31,8 @@ STATUS = {0: "SYLV_OK", 1: "SYLV_ERR_INVALID_ARG", 2: "SYLV_ERR_SHAPE", 3: "SYLV
 EXPORTED = ("sylv_plan_create", "sylv_plan_destroy", "sylv_workspace_size", "sylv_solve",
             "sylv_workspace_size_batched", "sylv_solve_batched", "sylv_forward", "sylv_sweep",
             "sylv_back", "sylv_residual", "sylv_plan_factors", "sylv_plan_set_timing",
-            "sylv_plan_timing", "sylv_schur", "sylv_status_string", "sylv_version")
+            "sylv_plan_timing", "sylv_schur", "sylv_status_string", "sylv_version",
+            "sylv_sweep_static")
 
 
 class SylvError(RuntimeError):
@@ -95,6 +96,8 @@ def _lib():
         for f in ("sylv_forward", "sylv_sweep", "sylv_back"):
             getattr(L, f).restype = st
             getattr(L, f).argtypes = [vp, vp, vp, ctypes.c_size_t, vp]
+        L.sylv_sweep_static.restype = st
+        L.sylv_sweep_static.argtypes = [vp, vp, vp]
         L.sylv_residual.restype = st
         L.sylv_residual.argtypes = [vp, vp, vp, vp, vp]
         L.sylv_plan_factors.restype = st
@@ -263,6 +266,13 @@ class Plan:
         wp, wb = self._wsargs(workspace)
         _check(_lib().sylv_sweep(self._h, _ptr(Tns), wp, wb, _stream_handle(stream)),
                "sylv_sweep")
+        return Tns
+
+    def sweep_static(self, Tns, stream=None):
+        """sylv_sweep_static: the sweep with the library's fixed scratch array
+        (no workspace, no allocation); see include/sylv.h for its limits."""
+        _check(_lib().sylv_sweep_static(self._h, _ptr(Tns), _stream_handle(stream)),
+               "sylv_sweep_static")
         return Tns
 
     def back(self, Tns, workspace=None, stream=None):

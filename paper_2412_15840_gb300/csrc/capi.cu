@@ -953,3 +953,55 @@ sylv_status sylv_plan_timing(sylv_plan_t p, sylv_timing *out, int reset) {
 }
 
 }  // extern "C"
+
+// ======================================================= scratch-free sweep ==
+// sylv_sweep_static serves callers that cannot allocate device memory (a fixed
+// budget already reserved by another allocator, or a loop where an allocation
+// would stall on a device synchronisation).  Its scratch is this array: one
+// per device that loads the library, held until the process exits.  Host code
+// must not hand `g_static_scratch` itself to a kernel (on the host it names a
+// host-side stand-in); the device address comes from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_static_scratch[SYLV_STATIC_SCRATCH_BYTES];
+
+namespace {
+constexpr int STATIC_MAX_DEVICES = 64;
+std::mutex g_static_mu;
+void *g_static_addr[STATIC_MAX_DEVICES] = {};
+
+// Device address of the array on `dev` (which must be current); looked up
+// once per device, on the first call there.
+sylv_status static_scratch(int dev, void **out) {
+    if (dev < 0 || dev >= STATIC_MAX_DEVICES) return SYLV_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_static_scratch) != cudaSuccess || !ptr) {
+            cudaGetLastError();
+            return SYLV_ERR_CUDA;
+        }
+        g_static_addr[dev] = ptr;
+    }
+    *out = g_static_addr[dev];
+    return SYLV_OK;
+}
+}  // namespace
+
+extern "C" sylv_status sylv_sweep_static(sylv_plan_t p, void *Tdev, void *stream) {
+    if (!p || !Tdev) return SYLV_ERR_INVALID_ARG;
+    const size_t cnt_off = align256(sizeof(DevFlags));
+    if (cnt_off + align256((size_t)p->sw.ntiles * 4) > SYLV_STATIC_SCRATCH_BYTES)
+        return SYLV_ERR_SHAPE;
+    DeviceGuard dg(p->device);
+    if (!dg.ok) return SYLV_ERR_CUDA;
+    void *base = nullptr;
+    sylv_status s = static_scratch(p->device, &base);
+    if (s != SYLV_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    Ctx c{p, st, reinterpret_cast<DevFlags *>(base),
+          reinterpret_cast<int *>((char *)base + cnt_off)};
+    // the array keeps the previous call's control block: clear it (done, err,
+    // ticket); run_sweep then rewrites every tile counter before the sweep
+    if (launch_solve_init(c.flags, st) != cudaSuccess) return SYLV_ERR_CUDA;
+    if (run_sweep(c, Tdev, p->fp64()) != cudaSuccess) return SYLV_ERR_CUDA;
+    return SYLV_OK;
+}
