@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-oracle", action="store_true",
                     help="skip the oracle error check and CPU baseline")
+    ap.add_argument("--kernels-once", action="store_true",
+                    help="run each hot-path kernel family once on the workload (for ncu)")
     return ap.parse_args()
 
 
@@ -164,6 +166,33 @@ def config_block():
 
 # ------------------------------------------------------------------- ours --
 
+def kernels_once(local: int) -> int:
+    """One launch group of every hot-path kernel family, in this order:
+    FP64 residual passes, FP32 forward passes, FP32 sweep, FP64 forward
+    passes, FP64 sweep (a short, fixed launch sequence for ncu captures)."""
+    import torch
+    from paper_2412_15840_gb300.build import build
+    build()
+    from paper_2412_15840_gb300 import Plan, to_device
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    p = si.random_problem(SHAPE, 1, seed=0, name="N4_n64")
+    m = Plan(A=p.A, nrhs=1, prec="mixed", device=local)
+    f = Plan(A=p.A, nrhs=1, prec="fp64", device=local)
+    B = to_device(p.B, device=dev)
+    X = B.clone()
+    R = torch.empty_like(B)
+    W = B.to(torch.complex64)
+    m.residual(B, X, R)
+    m.forward(W)
+    m.sweep(W)
+    f.forward(X)
+    f.sweep(X)
+    torch.cuda.synchronize(dev)
+    print("kernels-once ok")
+    return 0
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -171,6 +200,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.kernels_once:
+        return kernels_once(local)
 
     import torch
     import torch.distributed as dist
