@@ -90,7 +90,8 @@ struct sylv_plan_s {
     SweepArgs sw{};               // template; Y, T, flags filled per launch
     int sweep_grid = 1, sweep_threads = 256;
     size_t sweep_smem = 0;
-    int *d_order = nullptr, *d_sched = nullptr, *d_lev = nullptr;
+    int *d_order = nullptr, *d_sched = nullptr, *d_lev = nullptr, *d_sched_e = nullptr;
+    unsigned long long *d_coord = nullptr;
 
     double min_den = 0.0, max_den = 0.0;
     size_t off_cnt = 0, off_W = 0, off_R = 0, ws_bytes = 0;
@@ -180,10 +181,11 @@ sylv_status make_groups(const sylv_plan_s &p, bool fp64, bool composition, int g
 }
 
 sylv_status make_sweep(sylv_plan_s &p, const sylv_tuning *tu, std::vector<int> &order,
-                       std::vector<int> &sched, std::vector<int> &lev) {
+                       std::vector<int> &sched, std::vector<int> &lev, std::vector<int> &sched_e,
+                       std::vector<unsigned long long> &coord) {
     SweepArgs &a = p.sw;
     a.Nm = p.Nm;
-    const int target = p.fp64() ? 256 : 512;
+    const int target = p.fp64() ? 256 : 1024;   // entries per tile (measured on GB300)
     int b[MAXM];
     bool manual = false;
     for (int j = 0; j < p.Nm; ++j) {
@@ -218,6 +220,7 @@ sylv_status make_sweep(sylv_plan_s &p, const sylv_tuning *tu, std::vector<int> &
         a.n[j] = p.n[j];
         a.S[j] = p.S[j];
         a.b[j] = b[j];
+        a.qpos[j] = b[j] > 1 ? a.nin : -1;
         a.Bc[j] = (int)((p.n[j] + b[j] - 1) / b[j]);
         a.TS[j] = ts;
         ts *= a.Bc[j];
@@ -255,6 +258,32 @@ sylv_status make_sweep(sylv_plan_s &p, const sylv_tuning *tu, std::vector<int> &
         std::vector<int> pos(lev.begin(), lev.end() - 1);
         for (int e = 0; e < a.Pt; ++e) sched[pos[lvl[e]]++] = e;
     }
+    // for full tiles: the schedule as box offsets, and every box offset's
+    // in-tile coordinates packed 8 bits per mode
+    a.bmax = 1;
+    a.fast = a.nin <= 8 ? 1 : 0;
+    for (int q = 0; q < a.nin; ++q) {
+        a.bmax = std::max(a.bmax, a.b[a.inmode[q]]);
+        if (a.b[a.inmode[q]] > 255) a.fast = 0;
+    }
+    sched_e.assign(a.Pt, 0);
+    coord.assign(a.Pt, 0ull);
+    for (int qq = 0; qq < a.Pt; ++qq) {
+        int e = 0;
+        for (int q = 0; q < a.nin; ++q) {
+            const int bq = a.b[a.inmode[q]];
+            const int apq = (sched[qq] / a.BS[q]) % bq;
+            e += (bq - 1 - apq) * a.BS[q];
+        }
+        sched_e[qq] = e;
+    }
+    if (a.fast)
+        for (int e = 0; e < a.Pt; ++e) {
+            unsigned long long c = 0;
+            for (int q = 0; q < a.nin; ++q)
+                c |= (unsigned long long)((e / a.BS[q]) % a.b[a.inmode[q]]) << (8 * q);
+            coord[e] = c;
+        }
 
     // tile order: by level sum_j (Bc_j - 1 - I_j), then right-hand side, then id
     int maxlev = 0;
@@ -280,9 +309,17 @@ sylv_status make_sweep(sylv_plan_s &p, const sylv_tuning *tu, std::vector<int> &
             for (int64_t q = cnt[(size_t)l]; q < cnt[(size_t)l + 1]; ++q)
                 order[w++] = (int)(r * ts + by_level[(size_t)q]);
 
-    p.sweep_threads = (a.Pt >= 256) ? 256 : 128;
-    if (tu && tu->sweep_threads > 0) p.sweep_threads = tu->sweep_threads;
-    p.sweep_smem = (size_t)a.Pt * (p.fp64() ? 16 : 8);
+    p.sweep_threads = p.fp64() ? 128 : 256;
+    if (tu && tu->sweep_threads > 0) p.sweep_threads = std::min(256, (tu->sweep_threads + 31) / 32 * 32);
+    // FP64 reciprocals, tile values, one staged block of T
+    const size_t esz = p.fp64() ? 16 : 8;
+    int td = 0;
+    for (int q = 0; q < a.nin; ++q) {
+        a.tdoff[q] = td;
+        td += a.b[a.inmode[q]] * a.b[a.inmode[q]];
+    }
+    p.sweep_smem = (size_t)a.Pt * (esz + 16) + ((size_t)SWEEP_KCH * a.bmax + td) * esz;
+    if (p.sweep_smem > 200 * 1024) return SYLV_ERR_SHAPE;
     return SYLV_OK;
 }
 
@@ -400,6 +437,8 @@ cudaError_t run_sweep(Ctx &c, void *Y, bool fp64) {
     a.order = p->d_order;
     a.sched = p->d_sched;
     a.lev_start = p->d_lev;
+    a.sched_e = p->d_sched_e;
+    a.coord = p->d_coord;
     a.cnt = c.cnt;
     a.flags = c.flags;
     cudaError_t e = launch_sweep_init(a, c.st);
@@ -666,8 +705,9 @@ sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t 
     if (s != SYLV_OK) return s;
     s = make_groups(*p, true, false, gmax, p->rgroups);
     if (s != SYLV_OK) return s;
-    std::vector<int> order, sched, lev;
-    s = make_sweep(*p, tuning, order, sched, lev);
+    std::vector<int> order, sched, lev, sched_e;
+    std::vector<unsigned long long> coord;
+    s = make_sweep(*p, tuning, order, sched, lev, sched_e, coord);
     if (s != SYLV_OK) return s;
 
     // device pool: per mode Uh64 U64 A64 T64 d64 Uh32 U32 T32, then the tables
@@ -684,6 +724,8 @@ sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t 
     reserve(sched.size() * 4);
     reserve(lev.size() * 4);
     reserve(3 * sizeof(unsigned long long));
+    reserve(sched_e.size() * 4);
+    reserve(coord.size() * 8);
     size_t pool_bytes = align256(off);
     if (cudaMalloc(&p->dpool, pool_bytes) != cudaSuccess) {
         cudaGetLastError();
@@ -742,6 +784,10 @@ sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t 
     unsigned long long *dm = (unsigned long long *)(base + offs[oi + 3]);
     unsigned long long init3[3] = {~0ull, 0ull, 0ull};
     std::memcpy(host.data() + offs[oi + 3], init3, sizeof(init3));
+    std::memcpy(host.data() + offs[oi + 4], sched_e.data(), sched_e.size() * 4);
+    std::memcpy(host.data() + offs[oi + 5], coord.data(), coord.size() * 8);
+    p->d_sched_e = (int *)(base + offs[oi + 4]);
+    p->d_coord = (unsigned long long *)(base + offs[oi + 5]);
     if (cudaMemcpy(p->dpool, host.data(), pool_bytes, cudaMemcpyHostToDevice) != cudaSuccess)
         return SYLV_ERR_CUDA;
 
@@ -757,6 +803,8 @@ sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t 
     p->min_den = mn;
     p->max_den = mx;
     if (r3[2] != 0 || !(mn > 0.0) || !std::isfinite(mx)) return SYLV_ERR_SINGULAR;
+    // power of two centring |scale * sum|^2 on 1 for the sweep's reciprocals
+    p->sw.den_scale = std::ldexp(1.0, -(int)std::lround(0.5 * (std::log2(mn) + std::log2(mx))));
 
     // sweep grid: every SM holds as many tiles as fit
     {

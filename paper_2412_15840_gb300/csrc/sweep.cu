@@ -1,0 +1,409 @@
+// Triangular sweep of the transformed system sum_j T_j (x)_j Y = C
+// (Eq. (yi1i2iN), the second phase of Algorithm 3) on sm_103a.
+//
+// The entries are grouped in tiles: a box of b_j consecutive indices along
+// every mode.  Eq. (yi1i2iN) makes entry i depend on the entries that differ
+// from it in one mode and have a larger index there; at tile granularity,
+// tile I therefore needs the tiles I + m e_j (m >= 1) along every mode, and
+// waiting for the immediate successors I + e_j suffices (each of them waited
+// for its own successors).  A persistent grid takes tiles in the order of
+// their level sum_j (B_j - 1 - I_j) through an atomic ticket; before solving,
+// a tile waits (bounded) until a per-tile counter of unfinished immediate
+// successors reaches zero.  A CTA only ever waits on tiles with smaller
+// tickets, which running CTAs hold, so no co-residency is needed.
+//
+// One tile, three stages:
+//  1. load C, form the FP64 reciprocal of sigma + sum_j t_{j,i_j i_j} for
+//     every entry, then subtract the contributions of the solved tiles mode
+//     by mode as a small GEMM: T_j[rows of the block, later columns] times the
+//     strip of solved values.  One thread owns a fiber of the tile along mode
+//     j, loads every strip value once and applies all b_j rows of the T block
+//     (staged in shared memory) to it.
+//  2. solve the tile in place, level by level of the in-tile index sum
+//     measured from the tile's end: the in-tile part of Eq. (yi1i2iN), then
+//     y = num * (1/den) with the reciprocal formed in FP64 in stage 1.
+//  3. store Y (L2), fence, release the counters of the predecessor tiles.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "cplx.cuh"
+#include "sylv_internal.h"
+
+namespace sylv {
+
+constexpr int SW_KCH = SWEEP_KCH;
+constexpr int SW_RG = 8;     // fiber rows kept in registers at once
+
+// The reciprocal of a diagonal sum is formed in FP64 in stage 1 and applied in
+// the in-tile wavefront: as double2 on the FP64 path; on the FP32 path as the
+// pair hi = fl32(1/den), lo = fl32(1/den - hi), so that the wavefront, which is
+// latency-critical, issues no instruction on GB300's narrow FP64 pipe.
+template <typename real> struct InvT;
+template <> struct InvT<double> { using type = double2; };
+template <> struct InvT<float> { using type = float4; };
+
+__device__ __forceinline__ void store_inv(double2 r, double2 &o) { o = r; }
+__device__ __forceinline__ void store_inv(double2 r, float4 &o) {
+    const float hx = (float)r.x, hy = (float)r.y;
+    o = make_float4(hx, hy, (float)(r.x - (double)hx), (float)(r.y - (double)hy));
+}
+__device__ __forceinline__ double2 apply_inv(double2 n, double2 v) {
+    return make_double2(n.x * v.x - n.y * v.y, n.x * v.y + n.y * v.x);
+}
+__device__ __forceinline__ float2 apply_inv(float2 n, float4 v) {
+    float tx = fmaf(n.x, v.z, -n.y * v.w);      // n * lo first, then n * hi
+    float ty = fmaf(n.x, v.w, n.y * v.z);
+    tx = fmaf(-n.y, v.y, tx);
+    ty = fmaf(n.y, v.x, ty);
+    return make_float2(fmaf(n.x, v.x, tx), fmaf(n.x, v.y, ty));
+}
+
+template <typename real>
+__global__ void __launch_bounds__(256) k_sweep(const __grid_constant__ SweepArgs a) {
+    using C2 = typename C2T<real>::type;
+    using Inv = typename InvT<real>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Inv *inv_s = reinterpret_cast<Inv *>(smem_raw);
+    C2 *tile_s = reinterpret_cast<C2 *>(inv_s + a.Pt);
+    C2 *Ts = tile_s + a.Pt;                       // SW_KCH x bmax block of T_j
+    C2 *Td = Ts + SW_KCH * a.bmax;                // diagonal blocks of the in-tile modes
+    __shared__ int s_ticket, s_tile, s_abort, s_full;
+    __shared__ int64_t s_o[MAXM];
+    __shared__ int s_be[MAXM], s_cnt[MAXM], s_I[MAXM];
+    __shared__ int64_t s_gbase;
+    __shared__ double s_den0x, s_den0y;
+
+    if (*(volatile const int *)&a.flags->done) return;
+    C2 *Y = reinterpret_cast<C2 *>(a.Y);
+    const int Nm = a.Nm, nin = a.nin, nt = blockDim.x;
+
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int t = atomicAdd(&a.flags->ticket, 1);
+            s_ticket = t;
+            s_abort = 0;
+            if (t < a.ntiles) {
+                const int tile = a.order[t];
+                s_tile = tile;
+                volatile int *c = a.cnt + tile;
+                volatile int *err = &a.flags->err;
+                const long long t0 = clock64();
+                while (*c > 0) {
+                    if (*err) { s_abort = 1; break; }
+                    if (clock64() - t0 > a.timeout_cycles) {
+                        atomicOr(&a.flags->err, ERRBIT_TIMEOUT);
+                        s_abort = 1;
+                        break;
+                    }
+                    __nanosleep(100);
+                }
+                __threadfence();
+            }
+        }
+        __syncthreads();
+        if (s_ticket >= a.ntiles) break;
+        const int tile = s_tile;
+        if (s_abort) {
+            // drain: mark this tile finished so that nothing waits on it
+            if (threadIdx.x == 0) {
+                const int64_t rem = tile % a.ntiles1;
+                for (int j = 0; j < Nm; ++j) {
+                    const int Ij = (int)((rem / a.TS[j]) % a.Bc[j]);
+                    if (Ij > 0) atomicSub(a.cnt + tile - a.TS[j], 1);
+                }
+            }
+            __syncthreads();
+            continue;
+        }
+
+        // tile geometry
+        if (threadIdx.x == 0) {
+            const int64_t rhs = tile / a.ntiles1;
+            const int64_t rem = tile % a.ntiles1;
+            int64_t gb = rhs * a.ntot;
+            double dx = a.sig_re, dy = a.sig_im;
+            int full = 1;
+            for (int j = 0; j < Nm; ++j) {
+                const int Ij = (int)((rem / a.TS[j]) % a.Bc[j]);
+                const int64_t o = (int64_t)Ij * a.b[j];
+                int64_t be = a.n[j] - o;
+                if (be > a.b[j]) be = a.b[j];
+                else if (be < a.b[j]) full = 0;
+                s_I[j] = Ij;
+                s_o[j] = o;
+                s_be[j] = (int)be;
+                s_cnt[j] = (int)(a.n[j] - o - be);
+                gb += o * a.S[j];
+                if (a.b[j] == 1) {      // modes outside the tile: constant diagonal term
+                    dx += a.d[j][2 * o];
+                    dy += a.d[j][2 * o + 1];
+                }
+            }
+            s_gbase = gb;
+            s_den0x = dx;
+            s_den0y = dy;
+            s_full = full && a.fast;
+        }
+        __syncthreads();
+        const int64_t gbase = s_gbase;
+        const bool full = s_full != 0;
+
+        // stage 1a: C and the FP64 reciprocals of the diagonal sums
+        for (int e = threadIdx.x; e < a.Pt; e += nt) {
+            int64_t g = gbase;
+            bool ok = true;
+            double ex = s_den0x, ey = s_den0y;
+            if (full) {
+                const unsigned long long c = a.coord[e];
+                for (int q = 0; q < nin; ++q) {
+                    const int j = a.inmode[q];
+                    const int t = (int)((c >> (8 * q)) & 255u);
+                    g += (int64_t)t * a.S[j];
+                    const int64_t ij = s_o[j] + t;
+                    ex += a.d[j][2 * ij];
+                    ey += a.d[j][2 * ij + 1];
+                }
+            } else {
+                int r = e;
+                for (int q = 0; q < nin; ++q) {
+                    const int j = a.inmode[q];
+                    const int bj = a.b[j];
+                    const int t = r % bj;
+                    r /= bj;
+                    if (t >= s_be[j]) { ok = false; break; }
+                    g += (int64_t)t * a.S[j];
+                    const int64_t ij = s_o[j] + t;
+                    ex += a.d[j][2 * ij];
+                    ey += a.d[j][2 * ij + 1];
+                }
+            }
+            if (!ok) {
+                tile_s[e] = czero<C2>();
+                continue;
+            }
+            tile_s[e] = __ldcg(Y + g);
+            store_inv(crecip_scaled(ex, ey, a.den_scale), inv_s[e]);
+        }
+        // diagonal blocks T_j[o_j + r, o_j + c] (r < c < be_j) of the in-tile modes
+        for (int p = 0; p < nin; ++p) {
+            const int j = a.inmode[p];
+            const int bj = a.b[j], be = s_be[j];
+            const int64_t nj = a.n[j], oj = s_o[j];
+            const C2 *Tj = reinterpret_cast<const C2 *>(a.T[j]);
+            C2 *dst = Td + a.tdoff[p];
+            for (int idx = threadIdx.x; idx < be * be; idx += nt) {
+                const int r = idx % be, c = idx / be;
+                dst[r + c * bj] = __ldg(Tj + (oj + r) + (oj + c) * nj);
+            }
+        }
+        __syncthreads();
+
+        // stage 1b: contributions of the solved tiles, mode by mode
+        for (int j = 0; j < Nm; ++j) {
+            const int K = s_cnt[j];
+            if (K == 0) continue;
+            const int q = a.qpos[j];
+            const int bj = q >= 0 ? a.b[j] : 1;     // box extent along mode j
+            const int bej = s_be[j];                // valid rows of the block
+            const int bs = q >= 0 ? a.BS[q] : 1;
+            const int F = a.Pt / bj;                // fibers of the box along mode j
+            const int64_t nj = a.n[j], Sj = a.S[j], oj = s_o[j];
+            const int64_t kend = oj + bej;
+            const C2 *Tj = reinterpret_cast<const C2 *>(a.T[j]);
+            for (int k0 = 0; k0 < K; k0 += SW_KCH) {
+                const int kk = min(SW_KCH, K - k0);
+                for (int idx = threadIdx.x; idx < bej * kk; idx += nt) {
+                    const int r = idx % bej, c = idx / bej;
+                    Ts[c * bj + r] = __ldg(Tj + (oj + r) + (kend + k0 + c) * nj);
+                }
+                __syncthreads();
+                for (int f = threadIdx.x; f < F; f += nt) {
+                    const int e0 = (q >= 0) ? (f / bs) * (bs * bj) + (f % bs) : f;
+                    int64_t g0 = gbase;
+                    bool ok = true;
+                    if (full) {
+                        const unsigned long long c = a.coord[e0];
+                        for (int p = 0; p < nin; ++p)
+                            g0 += (int64_t)((c >> (8 * p)) & 255u) * a.S[a.inmode[p]];
+                    } else {
+                        int r = e0;
+                        for (int p = 0; p < nin; ++p) {
+                            const int jj = a.inmode[p];
+                            const int b = a.b[jj];
+                            const int t = r % b;
+                            r /= b;
+                            if (t >= s_be[jj]) { ok = false; break; }
+                            g0 += (int64_t)t * a.S[jj];
+                        }
+                    }
+                    if (!ok) continue;
+                    const C2 *ybase = Y + g0 + (kend + k0 - oj) * Sj;
+                    const int ncol = kk;
+                    for (int rg = 0; rg < bej; rg += SW_RG) {
+                        C2 acc[SW_RG];
+#pragma unroll
+                        for (int r = 0; r < SW_RG; ++r) acc[r] = czero<C2>();
+                        const C2 *yp = ybase;
+                        const C2 *tc = Ts + rg;
+                        int c = 0;
+                        for (; c + 4 <= ncol; c += 4) {
+                            const C2 y0 = __ldcg(yp), y1 = __ldcg(yp + Sj);
+                            const C2 y2 = __ldcg(yp + 2 * Sj), y3 = __ldcg(yp + 3 * Sj);
+                            yp += 4 * Sj;
+#pragma unroll
+                            for (int r = 0; r < SW_RG; ++r) {
+                                if (rg + r < bej) {
+                                    cmsub(acc[r], tc[r], y0);
+                                    cmsub(acc[r], tc[bj + r], y1);
+                                    cmsub(acc[r], tc[2 * bj + r], y2);
+                                    cmsub(acc[r], tc[3 * bj + r], y3);
+                                }
+                            }
+                            tc += 4 * bj;
+                        }
+                        for (; c < ncol; ++c) {
+                            const C2 y = __ldcg(yp);
+                            yp += Sj;
+#pragma unroll
+                            for (int r = 0; r < SW_RG; ++r)
+                                if (rg + r < bej) cmsub(acc[r], tc[r], y);
+                            tc += bj;
+                        }
+#pragma unroll
+                        for (int r = 0; r < SW_RG; ++r) {
+                            if (rg + r < bej) {
+                                C2 &v = tile_s[e0 + (rg + r) * bs];
+                                v.x += acc[r].x;
+                                v.y += acc[r].y;
+                            }
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+
+        // stage 2: in-tile wavefront over index sums measured from the tile's end
+        for (int lev = 0; lev < a.Lin; ++lev) {
+            const int q0 = a.lev_start[lev], q1 = a.lev_start[lev + 1];
+            for (int qq = q0 + threadIdx.x; qq < q1; qq += nt) {
+                int e = 0;
+                unsigned long long c = 0;
+                if (full) {
+                    e = a.sched_e[qq];
+                    c = a.coord[e];
+                } else {
+                    int r = a.sched[qq];
+                    bool ok = true;
+                    for (int p = 0; p < nin; ++p) {
+                        const int j = a.inmode[p];
+                        const int bj = a.b[j];
+                        const int apj = r % bj;
+                        r /= bj;
+                        if (apj >= s_be[j]) { ok = false; break; }
+                        e += (s_be[j] - 1 - apj) * a.BS[p];
+                    }
+                    if (!ok) continue;
+                }
+                C2 num = tile_s[e];
+                for (int p = 0; p < nin; ++p) {
+                    const int j = a.inmode[p];
+                    const int bs = a.BS[p];
+                    const int t = full ? (int)((c >> (8 * p)) & 255u) : (e / bs) % a.b[j];
+                    const int be = s_be[j];
+                    if (t + 1 >= be) continue;
+                    const int bj = a.b[j];
+                    const C2 *tp = Td + a.tdoff[p] + t + (t + 1) * bj;
+                    const C2 *yp = tile_s + e + bs;
+                    for (int tt = t + 1; tt < be; ++tt) {     // in-tile successors
+                        cmsub(num, *tp, *yp);
+                        tp += bj;
+                        yp += bs;
+                    }
+                }
+                tile_s[e] = apply_inv(num, inv_s[e]);
+            }
+            __syncthreads();
+        }
+
+        // stage 3: store Y and release the tiles that wait on this one
+        for (int e = threadIdx.x; e < a.Pt; e += nt) {
+            int64_t g = gbase;
+            bool ok = true;
+            if (full) {
+                const unsigned long long c = a.coord[e];
+                for (int p = 0; p < nin; ++p)
+                    g += (int64_t)((c >> (8 * p)) & 255u) * a.S[a.inmode[p]];
+            } else {
+                int r = e;
+                for (int p = 0; p < nin; ++p) {
+                    const int j = a.inmode[p];
+                    const int bj = a.b[j];
+                    const int t = r % bj;
+                    r /= bj;
+                    if (t >= s_be[j]) { ok = false; break; }
+                    g += (int64_t)t * a.S[j];
+                }
+            }
+            if (ok) __stcg(Y + g, tile_s[e]);
+        }
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int j = 0; j < Nm; ++j)
+                if (s_I[j] > 0) atomicSub(a.cnt + tile - a.TS[j], 1);
+        }
+    }
+}
+
+__global__ void k_sweep_init(const __grid_constant__ SweepArgs a) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.flags->ticket = 0;
+    for (int64_t tile = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; tile < a.ntiles;
+         tile += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t rem = tile % a.ntiles1;
+        int c = 0;
+        for (int j = 0; j < a.Nm; ++j) {
+            const int Ij = (int)((rem / a.TS[j]) % a.Bc[j]);
+            c += (Ij < a.Bc[j] - 1);
+        }
+        a.cnt[tile] = c;
+    }
+}
+
+cudaError_t launch_sweep(int fp64, const SweepArgs &a, int grid, int threads, size_t smem,
+                         cudaStream_t st) {
+    if (a.ntiles <= 0) return cudaSuccess;
+    if (fp64)
+        k_sweep<double><<<grid, threads, smem, st>>>(a);
+    else
+        k_sweep<float><<<grid, threads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_init(const SweepArgs &a, cudaStream_t st) {
+    int64_t blocks = (a.ntiles + 255) / 256;
+    if (blocks < 1) blocks = 1;
+    if (blocks > 4096) blocks = 4096;
+    k_sweep_init<<<(unsigned)blocks, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+int sweep_blocks_per_sm(int fp64, int threads, size_t smem) {
+    int nb = 0;
+    cudaError_t e = fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep<double>,
+                                                                         threads, smem)
+                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep<float>,
+                                                                         threads, smem);
+    return e == cudaSuccess ? nb : 0;
+}
+
+cudaError_t sweep_init_attrs() {
+    cudaError_t e = cudaFuncSetAttribute(k_sweep<double>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_sweep<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                200 * 1024);
+}
+
+}  // namespace sylv

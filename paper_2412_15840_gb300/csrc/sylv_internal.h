@@ -16,6 +16,7 @@ namespace sylv {
 constexpr int MAXM = 40;   // modes with n_j > 1 (after singleton removal)
 constexpr int MAXG = 16;   // modes fused into one transform pass
 constexpr int MAX_N = 1024;
+constexpr int SWEEP_KCH = 64;  // columns of T_j staged per chunk by the sweep
 
 sylv_status schur_host(int64_t n, const double *A, double *Q, double *T);
 
@@ -65,6 +66,9 @@ struct SweepArgs {
     int nin;                  // modes with block > 1 (inside a tile)
     int Lin;                  // in-tile levels
     int Pt;                   // entries of a full tile
+    int bmax;                 // largest in-tile block extent
+    int fast;                 // packed coordinates available (<= 8 in-tile modes, b <= 255)
+    double den_scale;         // power of two keeping |scale * diagonal sum|^2 in range
     int64_t n[MAXM];
     int64_t S[MAXM];          // element strides
     int64_t TS[MAXM];         // tile-index strides
@@ -72,6 +76,8 @@ struct SweepArgs {
     int Bc[MAXM];             // blocks per mode
     int inmode[MAXM];         // indices of in-tile modes
     int BS[MAXM];             // box strides of in-tile modes (by position in inmode)
+    int tdoff[MAXM];          // offset of each in-tile mode's b x b diagonal block of T
+    int qpos[MAXM];           // position of mode j in inmode, or -1
     const void *T[MAXM];      // T_j, compute precision, column-major
     const double *d[MAXM];    // diag(T_j) as interleaved FP64 pairs
     double sig_re, sig_im;
@@ -80,6 +86,8 @@ struct SweepArgs {
     int *cnt;                 // per-tile count of unfinished immediate successors
     DevFlags *flags;
     const int *sched;         // in-tile schedule (a'-linear offsets by level)
+    const int *sched_e;       // the same schedule as box offsets, for full tiles
+    const unsigned long long *coord;  // per box offset: in-tile coordinates, 8 bits each
     const int *lev_start;     // Lin + 1 entries
     long long timeout_cycles;
 };
@@ -97,6 +105,7 @@ cudaError_t launch_den_minmax(int Nm, const int64_t *n, const double *const *d, 
                               double sig_im, int64_t ntot, unsigned long long *out3,
                               cudaStream_t st);
 cudaError_t kernels_init(int device);
+cudaError_t sweep_init_attrs();
 int sweep_blocks_per_sm(int fp64, int threads, size_t smem);
 #endif
 
