@@ -95,7 +95,8 @@ typedef struct {
     int32_t block[64];
     int32_t group_max;
     int32_t sweep_threads;    /* 0 = automatic */
-    int32_t reserved[6];
+    int32_t no_tensor_cores;  /* 1 = FP32 transforms on CUDA cores only */
+    int32_t reserved[5];
 } sylv_tuning;
 
 /*

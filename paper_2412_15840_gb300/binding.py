@@ -59,7 +59,8 @@ class Timing(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int32 * 64), ("group_max", ctypes.c_int32),
-                ("sweep_threads", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("sweep_threads", ctypes.c_int32), ("no_tensor_cores", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 _LIB = None
@@ -178,7 +179,7 @@ class Plan:
                  T: Optional[Sequence] = None, nrhs: int = 1, prec: str = "fp64",
                  rtol: float = 1e-10, max_refine: int = 5, device: int = 0,
                  block: Optional[Sequence[int]] = None, group_max: int = 0,
-                 sweep_threads: int = 0):
+                 sweep_threads: int = 0, tensor_cores: bool = True):
         L = _lib()
         if (A is None) == (Q is None or T is None):
             raise ValueError("give A, or both Q and T")
@@ -200,13 +201,14 @@ class Plan:
         pQ = ptrs(Q) if Q is not None else None
         pT = ptrs(T) if T is not None else None
         tun = None
-        if block is not None or group_max or sweep_threads:
+        if block is not None or group_max or sweep_threads or not tensor_cores:
             tun = Tuning()
             if block is not None:
                 for j, b in enumerate(block):
                     tun.block[j] = int(b)
             tun.group_max = int(group_max)
             tun.sweep_threads = int(sweep_threads)
+            tun.no_tensor_cores = 0 if tensor_cores else 1
         h = vp()
         s = L.sylv_plan_create(ctypes.byref(h), self.N, n, self.nrhs, pA, pQ, pT, self.prec,
                                float(rtol), int(max_refine), int(device),

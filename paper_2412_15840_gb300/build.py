@@ -2,7 +2,7 @@
 
     python -m paper_2412_15840_gb300.build [--force] [--debug]
 
-Four translation units compiled in parallel (nvcc for the CUDA sources, the
+Five translation units compiled in parallel (nvcc for the CUDA sources, the
 host C++ Schur code through nvcc's host compiler), one -gencode, static
 cudart, linked into paper_2412_15840_gb300/libsylv.so.  No cmake.
 """
@@ -20,7 +20,7 @@ LIB = os.path.join(PKG, "libsylv.so")
 BUILD = os.path.join(PKG, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels.cu", "sweep.cu", "capi.cu", "schur.cpp"]
+SOURCES = ["kernels.cu", "sweep.cu", "modeprod_tc.cu", "capi.cu", "schur.cpp"]
 HEADERS = ["sylv_internal.h", "cplx.cuh", os.path.join("..", "..", "include", "sylv.h")]
 
 

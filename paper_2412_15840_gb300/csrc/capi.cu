@@ -27,7 +27,30 @@ struct Group {
     int Lt = 1, Rt = 1;
     int64_t tilesL = 1;
     size_t smem = 0;
+    // tensor-core pass (one mode): operand geometry and the B images of
+    // U^* (forward) and U (back) in the device pool
+    int tc = 0;
+    int Kp = 0, Np = 0, sboA = 0, sboB = 0, bimg_bytes = 0, tmem_cols = 0;
+    const unsigned char *img[2] = {nullptr, nullptr};
 };
+
+// A mode runs on the tensor cores when its tile holds 64 complex positions
+// along the preceding modes and the operands fit in shared memory.
+bool tc_mode_ok(int64_t L, int64_t n) { return L >= 64 && n >= 32 && n <= 80; }
+
+void tc_geometry(Group &g, int n) {
+    g.tc = 1;
+    g.Kp = (n + 7) / 8 * 8;
+    g.Np = (2 * n + 15) / 16 * 16;
+    g.sboB = g.Kp * 32;
+    g.sboA = g.Kp * 32 + 16;                   // padding: conflict-free staging stores
+    g.bimg_bytes = (g.Np / 8) * g.sboB;
+    int need = std::max(g.Np, n + 16 * ((n + 15) / 16));
+    int cols = 32;
+    while (cols < need) cols *= 2;
+    g.tmem_cols = cols;
+    g.smem = (size_t)2 * g.bimg_bytes + (size_t)2 * 16 * g.sboA;
+}
 
 struct TimedPhase {
     int phase;
@@ -89,6 +112,7 @@ struct sylv_plan_s {
 
     SweepArgs sw{};               // template; Y, T, flags filled per launch
     int sweep_grid = 1, sweep_threads = 256;
+    int num_sms = 1;
     size_t sweep_smem = 0;
     int *d_order = nullptr, *d_sched = nullptr, *d_lev = nullptr, *d_sched_e = nullptr;
     unsigned long long *d_coord = nullptr;
@@ -141,6 +165,7 @@ bool choose_tile(int64_t L, int64_t P, int64_t R, int64_t Et, int64_t Eh, int &L
 }
 
 sylv_status make_groups(const sylv_plan_s &p, bool fp64, bool composition, int group_max,
+                        bool allow_tc,
                         std::vector<Group> &out) {
     const int64_t esz = fp64 ? 16 : 8;
     const int64_t Et = fp64 ? 2048 : 4096;
@@ -156,17 +181,29 @@ sylv_status make_groups(const sylv_plan_s &p, bool fp64, bool composition, int g
         out.push_back(g);
         return SYLV_OK;
     }
+    const bool use_tc = composition && !fp64 && allow_tc;
     int j = 0;
     while (j < p.Nm) {
         Group g;
         g.first = j;
         g.L = p.S[j];
+        if (use_tc && tc_mode_ok(g.L, p.n[j])) {
+            g.count = 1;
+            g.P = p.n[j];
+            g.R = tot / (g.L * g.P);
+            g.tilesL = (g.L + 63) / 64;
+            tc_geometry(g, (int)p.n[j]);
+            out.push_back(g);
+            j += 1;
+            continue;
+        }
         int64_t Pcap = Et / std::min<int64_t>(g.L, 32);
         if (group_max > 0) Pcap = std::min<int64_t>(Pcap, group_max);
         g.P = p.n[j];
         g.count = 1;
         while (j + g.count < p.Nm && g.count < MAXG && g.P * p.n[j + g.count] <= Pcap &&
-               p.S[j + g.count] == g.L * g.P)
+               p.S[j + g.count] == g.L * g.P &&
+               !(use_tc && tc_mode_ok(p.S[j + g.count], p.n[j + g.count])))
             g.P *= p.n[j + g.count], g.count++;
         g.R = tot / (g.L * g.P);
         if (!choose_tile(g.L, g.P, g.R, Et, Eh, g.Lt, g.Rt)) return SYLV_ERR_SHAPE;
@@ -392,6 +429,26 @@ cudaError_t run_groups(Ctx &c, const std::vector<Group> &gs, bool fp64, int whic
         int out_kind = last ? last_out_kind : work_kind;
         int epi = last ? last_epi : EPI_STORE;
         if (g.count == 0 && a.in == a.out && epi == EPI_STORE) continue;   // identity
+        if (g.tc) {
+            if (in_kind != ELEM_C64) return cudaErrorInvalidValue;
+            TCArgs t{};
+            t.in = reinterpret_cast<const float *>(a.in);
+            t.out = a.out;
+            t.bimg = g.img[which];
+            t.n = (int)g.P;
+            t.Kp = g.Kp; t.Np = g.Np; t.sboA = g.sboA; t.sboB = g.sboB;
+            t.bimg_bytes = g.bimg_bytes;
+            t.tmem_cols = g.tmem_cols;
+            t.L = g.L; t.R = g.R; t.tilesL = g.tilesL;
+            t.flags = c.flags;
+            t.done = done;
+            const int64_t tiles = g.tilesL * g.R;
+            const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, p->num_sms));
+            cudaError_t e = launch_modeprod_tc(epi, t, grid, g.smem, c.st);
+            if (e != cudaSuccess) return e;
+            count(c);
+            continue;
+        }
         cudaError_t e = launch_modeprod(fp64, in_kind, out_kind, epi, a, g.smem, c.st);
         if (e != cudaSuccess) return e;
         count(c);
@@ -701,9 +758,10 @@ sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t 
 
     // transform and residual passes
     const int gmax = tuning ? tuning->group_max : 0;
-    sylv_status s = make_groups(*p, p->fp64(), true, gmax, p->tgroups);
+    const bool allow_tc = !(tuning && tuning->no_tensor_cores);
+    sylv_status s = make_groups(*p, p->fp64(), true, gmax, allow_tc, p->tgroups);
     if (s != SYLV_OK) return s;
-    s = make_groups(*p, true, false, gmax, p->rgroups);
+    s = make_groups(*p, true, false, gmax, false, p->rgroups);
     if (s != SYLV_OK) return s;
     std::vector<int> order, sched, lev, sched_e;
     std::vector<unsigned long long> coord;
@@ -726,6 +784,12 @@ sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t 
     reserve(3 * sizeof(unsigned long long));
     reserve(sched_e.size() * 4);
     reserve(coord.size() * 8);
+    const size_t tc_first = offs.size();
+    for (auto &g : p->tgroups)
+        if (g.tc) {
+            reserve((size_t)2 * g.bimg_bytes);     // U^*: hi, lo
+            reserve((size_t)2 * g.bimg_bytes);     // U: hi, lo
+        }
     size_t pool_bytes = align256(off);
     if (cudaMalloc(&p->dpool, pool_bytes) != cudaSuccess) {
         cudaGetLastError();
@@ -788,6 +852,43 @@ sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t 
     std::memcpy(host.data() + offs[oi + 5], coord.data(), coord.size() * 8);
     p->d_sched_e = (int *)(base + offs[oi + 4]);
     p->d_coord = (unsigned long long *)(base + offs[oi + 5]);
+    // tensor-core B operands: B[k, i] = Re M[i, k], B[k, n + i] = Im M[i, k]
+    // (M = U^* forward, U back), split into TF32 hi and lo, in the K-major
+    // no-swizzle layout the kernel's descriptors describe
+    {
+        size_t ti = tc_first;
+        for (auto &g : p->tgroups) {
+            if (!g.tc) continue;
+            const int j = g.first, n = (int)p->n[j];
+            const auto &Qj = p->Qh[p->orig[j]];
+            for (int dir = 0; dir < 2; ++dir) {
+                unsigned char *hi = reinterpret_cast<unsigned char *>(host.data()) + offs[ti + dir];
+                unsigned char *lo = hi + g.bimg_bytes;
+                for (int ii = 0; ii < g.Np; ++ii)
+                    for (int k = 0; k < g.Kp; ++k) {
+                        float v = 0.f;
+                        if (k < n && ii < 2 * n) {
+                            const int i = ii < n ? ii : ii - n;
+                            const cd m = dir == 0 ? std::conj(Qj[(size_t)(k + i * n)])
+                                                  : Qj[(size_t)(i + k * n)];
+                            v = (float)(ii < n ? m.real() : m.imag());
+                        }
+                        uint32_t u;
+                        std::memcpy(&u, &v, 4);
+                        if ((u & 0x7f800000u) != 0x7f800000u) u = (u + 0x1000u) & 0xffffe000u;
+                        float h;
+                        std::memcpy(&h, &u, 4);
+                        const float l = v - h;
+                        const size_t off = (size_t)(ii / 8) * g.sboB + (size_t)(k / 4) * 128 +
+                                           (size_t)(ii % 8) * 16 + (size_t)(k % 4) * 4;
+                        std::memcpy(hi + off, &h, 4);
+                        std::memcpy(lo + off, &l, 4);
+                    }
+                g.img[dir] = (const unsigned char *)(base + offs[ti + dir]);
+            }
+            ti += 2;
+        }
+    }
     if (cudaMemcpy(p->dpool, host.data(), pool_bytes, cudaMemcpyHostToDevice) != cudaSuccess)
         return SYLV_ERR_CUDA;
 
@@ -810,6 +911,7 @@ sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t 
     {
         int sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+        p->num_sms = std::max(1, sms);
         int per = sweep_blocks_per_sm(p->fp64(), p->sweep_threads, p->sweep_smem);
         if (per < 1) per = 1;
         int64_t grid = (int64_t)sms * per;

@@ -362,6 +362,7 @@ cudaError_t kernels_init(int) {
     if ((e = set_smem_attr<float, float2, float2, EPI_STORE>()) != cudaSuccess) return e;
     if ((e = set_smem_attr<float, float2, double2, EPI_STORE_NORM>()) != cudaSuccess) return e;
     if ((e = set_smem_attr<float, float2, double2, EPI_ACCUM>()) != cudaSuccess) return e;
+    if ((e = modeprod_tc_init_attrs()) != cudaSuccess) return e;
     return sweep_init_attrs();
 }
 

@@ -92,7 +92,23 @@ struct SweepArgs {
     long long timeout_cycles;
 };
 
+// Tensor-core (tcgen05, 3xTF32) transform pass over one mode, complex64 in.
+struct TCArgs {
+    const float *in;              // complex64 tensor, interleaved floats
+    void *out;                    // complex64, or complex128 for the last back pass
+    const unsigned char *bimg;    // B_hi image followed by B_lo image (shared-memory layout)
+    int n, Kp, Np;                // mode size, K padded to 8, N = 2n padded to 16
+    int sboA, sboB;               // 8-row group strides of the A and B operands (bytes)
+    int bimg_bytes;               // bytes of one B image
+    int tmem_cols;                // TMEM columns allocated (power of two >= 32)
+    int64_t L, R, tilesL;         // view (L, n, R); tiles of 64 l along L
+    DevFlags *flags;
+    const int *done;
+};
+
 #ifdef __CUDACC__
+cudaError_t launch_modeprod_tc(int epi, const TCArgs &a, int grid, size_t smem, cudaStream_t st);
+cudaError_t modeprod_tc_init_attrs();
 cudaError_t launch_modeprod(int fp64, int in_kind, int out_kind, int epi, const MPArgs &a,
                             size_t smem, cudaStream_t st);
 cudaError_t launch_sweep(int fp64, const SweepArgs &a, int grid, int threads, size_t smem,
