@@ -96,7 +96,11 @@ typedef struct {
     int32_t group_max;
     int32_t sweep_threads;    /* 0 = automatic */
     int32_t no_tensor_cores;  /* 1 = FP32 transforms on CUDA cores only */
-    int32_t reserved[5];
+    int32_t timeout_ms;       /* limit of each device-side dependency wait (0 = 2000) */
+    int32_t fault_tile;       /* test hook: k > 0 makes the sweep never release the
+                                 predecessors of its (k-1)-th tile, so that their waits
+                                 run out and the solve reports SYLV_ERR_TIMEOUT */
+    int32_t reserved[3];
 } sylv_tuning;
 
 /*
@@ -147,10 +151,16 @@ sylv_status sylv_solve(sylv_plan_t plan, const void *B_dev, void *X_dev, void *w
 
 /*
  * sylv_solve_batched -- `count` independent equations (any shapes) in one
- * call; the whole sequence is recorded once into a CUDA graph per argument
- * set and replayed.  plans[e], B_dev[e], X_dev[e] as for sylv_solve; the
- * workspace must hold sylv_workspace_size_batched bytes.  infos may be NULL,
- * else an array of `count` reports (the call then synchronises).
+ * call.  The equations' launch sequences are recorded once per argument set
+ * (plans, tensors, workspace) into a CUDA graph, spread over up to 8 forked
+ * streams so that small equations run concurrently, and replayed by one
+ * graph launch on `stream` on every later call with the same arguments.
+ * plans[e], B_dev[e], X_dev[e] as for sylv_solve (one device for all plans);
+ * the workspace must hold sylv_workspace_size_batched bytes.  infos may be
+ * NULL, else an array of `count` reports (the call then synchronises).  A
+ * plan with phase timing enabled makes the call launch directly, in order.
+ * The first call with a new argument set must not happen during a stream
+ * capture of the caller's own.
  */
 sylv_status sylv_workspace_size_batched(int count, const sylv_plan_t *plans, size_t *bytes);
 sylv_status sylv_solve_batched(int count, const sylv_plan_t *plans, const void *const *B_dev,
@@ -203,6 +213,21 @@ sylv_status sylv_residual(sylv_plan_t plan, const void *B_dev, const void *X_dev
  */
 #define SYLV_STATIC_SCRATCH_BYTES (1u << 20)
 sylv_status sylv_sweep_static(sylv_plan_t plan, void *T_dev, void *stream);
+
+/*
+ * sylv_plan_autotune -- measure candidate tilings of the triangular sweep on
+ * this device (tile extents from ~64 to ~2048 entries, 128 or 256 threads
+ * per CTA) for the plan's own shape and keep the fastest.  T_dev: scratch
+ * tensor in the plan's working precision (complex128 for SYLV_FP64, complex64
+ * for SYLV_MIXED_FP32), overwritten with zeros and sweep results; workspace as
+ * for sylv_solve.  The workspace size of the plan does not change.  On
+ * return block_out[j] (nullable, N entries) holds the chosen extent along
+ * input mode j and *best_ms (nullable) the measured sweep time.
+ * Synchronises `stream`.
+ */
+sylv_status sylv_plan_autotune(sylv_plan_t plan, void *T_dev, void *workspace,
+                               size_t workspace_bytes, void *stream, int32_t *block_out,
+                               float *best_ms);
 
 /* The plan's Schur factors of input mode j (host copies; Q is the identity
  * 1x1 for a singleton).  Q_out and T_out hold n_j*n_j complex128 each. */

@@ -32,7 +32,7 @@ EXPORTED = ("sylv_plan_create", "sylv_plan_destroy", "sylv_workspace_size", "syl
             "sylv_workspace_size_batched", "sylv_solve_batched", "sylv_forward", "sylv_sweep",
             "sylv_back", "sylv_residual", "sylv_plan_factors", "sylv_plan_set_timing",
             "sylv_plan_timing", "sylv_schur", "sylv_status_string", "sylv_version",
-            "sylv_sweep_static")
+            "sylv_sweep_static", "sylv_plan_autotune")
 
 
 class SylvError(RuntimeError):
@@ -60,7 +60,8 @@ class Timing(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int32 * 64), ("group_max", ctypes.c_int32),
                 ("sweep_threads", ctypes.c_int32), ("no_tensor_cores", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("timeout_ms", ctypes.c_int32), ("fault_tile", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 _LIB = None
@@ -97,6 +98,10 @@ def _lib():
         for f in ("sylv_forward", "sylv_sweep", "sylv_back"):
             getattr(L, f).restype = st
             getattr(L, f).argtypes = [vp, vp, vp, ctypes.c_size_t, vp]
+        L.sylv_plan_autotune.restype = st
+        L.sylv_plan_autotune.argtypes = [vp, vp, vp, ctypes.c_size_t, vp,
+                                         ctypes.POINTER(ctypes.c_int32),
+                                         ctypes.POINTER(ctypes.c_float)]
         L.sylv_sweep_static.restype = st
         L.sylv_sweep_static.argtypes = [vp, vp, vp]
         L.sylv_residual.restype = st
@@ -179,7 +184,8 @@ class Plan:
                  T: Optional[Sequence] = None, nrhs: int = 1, prec: str = "fp64",
                  rtol: float = 1e-10, max_refine: int = 5, device: int = 0,
                  block: Optional[Sequence[int]] = None, group_max: int = 0,
-                 sweep_threads: int = 0, tensor_cores: bool = True):
+                 sweep_threads: int = 0, tensor_cores: bool = True, timeout_ms: int = 0,
+                 fault_tile: int = 0):
         L = _lib()
         if (A is None) == (Q is None or T is None):
             raise ValueError("give A, or both Q and T")
@@ -201,7 +207,8 @@ class Plan:
         pQ = ptrs(Q) if Q is not None else None
         pT = ptrs(T) if T is not None else None
         tun = None
-        if block is not None or group_max or sweep_threads or not tensor_cores:
+        if block is not None or group_max or sweep_threads or not tensor_cores or timeout_ms \
+                or fault_tile:
             tun = Tuning()
             if block is not None:
                 for j, b in enumerate(block):
@@ -209,6 +216,8 @@ class Plan:
             tun.group_max = int(group_max)
             tun.sweep_threads = int(sweep_threads)
             tun.no_tensor_cores = 0 if tensor_cores else 1
+            tun.timeout_ms = int(timeout_ms)
+            tun.fault_tile = int(fault_tile)
         h = vp()
         s = L.sylv_plan_create(ctypes.byref(h), self.N, n, self.nrhs, pA, pQ, pT, self.prec,
                                float(rtol), int(max_refine), int(device),
@@ -290,6 +299,20 @@ class Plan:
         _check(_lib().sylv_residual(self._h, _ptr(B), _ptr(X), _ptr(R), _stream_handle(stream)),
                "sylv_residual")
         return R
+
+    def autotune(self, scratch=None, workspace=None, stream=None):
+        """sylv_plan_autotune: time candidate sweep tilings, keep the fastest.
+        Returns (block extents per input mode, best sweep time in ms)."""
+        import torch
+        if scratch is None:
+            dt = torch.complex128 if self.prec == SYLV_FP64 else torch.complex64
+            scratch = torch.empty(self.numel, dtype=dt, device=f"cuda:{self.device}")
+        wp, wb = self._wsargs(workspace)
+        blk = (ctypes.c_int32 * self.N)()
+        ms = ctypes.c_float()
+        _check(_lib().sylv_plan_autotune(self._h, _ptr(scratch), wp, wb, _stream_handle(stream),
+                                         blk, ctypes.byref(ms)), "sylv_plan_autotune")
+        return tuple(int(b) for b in blk), float(ms.value)
 
     def factors(self, j: int):
         n = self.shape[j]

@@ -58,6 +58,14 @@ struct TimedPhase {
     int launches;
 };
 
+// One sweep configuration: kernel arguments (tables in `dbuf`), launch shape.
+struct SweepConfig {
+    SweepArgs a{};
+    int threads = 256, grid = 1;
+    size_t smem = 0;
+    void *dbuf = nullptr;
+};
+
 struct DeviceGuard {
     int prev = -1;
     bool ok = false;
@@ -110,12 +118,12 @@ struct sylv_plan_s {
     std::vector<Group> tgroups;   // transform passes in the working precision
     std::vector<Group> rgroups;   // FP64 residual passes
 
-    SweepArgs sw{};               // template; Y, T, flags filled per launch
-    int sweep_grid = 1, sweep_threads = 256;
+    SweepConfig sweep;            // Y, T, diag, flags, counters filled per launch
+    int64_t cnt_capacity = 0;     // tile counters the workspace holds (any tuned tiling)
+    double den_scale = 1.0;       // power of two for the sweep's reciprocals
     int num_sms = 1;
-    size_t sweep_smem = 0;
-    int *d_order = nullptr, *d_sched = nullptr, *d_lev = nullptr, *d_sched_e = nullptr;
-    unsigned long long *d_coord = nullptr;
+    long long timeout_cycles = 4000000000LL;   // per dependency wait
+    int fault_tile = -1;                       // test hook (sylv_tuning.fault_tile - 1)
 
     double min_den = 0.0, max_den = 0.0;
     size_t off_cnt = 0, off_W = 0, off_R = 0, ws_bytes = 0;
@@ -133,6 +141,7 @@ struct sylv_plan_s {
         for (auto &p : tphases) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
         for (auto e : ev_free) cudaEventDestroy(e);
         if (dpool) cudaFree(dpool);
+        if (sweep.dbuf) cudaFree(sweep.dbuf);
         if (cur >= 0 && cur != device) cudaSetDevice(cur);
     }
 
@@ -217,13 +226,9 @@ sylv_status make_groups(const sylv_plan_s &p, bool fp64, bool composition, int g
     return SYLV_OK;
 }
 
-sylv_status make_sweep(sylv_plan_s &p, const sylv_tuning *tu, std::vector<int> &order,
-                       std::vector<int> &sched, std::vector<int> &lev, std::vector<int> &sched_e,
-                       std::vector<unsigned long long> &coord) {
-    SweepArgs &a = p.sw;
-    a.Nm = p.Nm;
-    const int target = p.fp64() ? 256 : 1024;   // entries per tile (measured on GB300)
-    int b[MAXM];
+// Sweep tile extents: balanced doubling of the block with the most blocks
+// left until a tile holds `target` entries (or the explicit tuning blocks).
+void choose_blocks(const sylv_plan_s &p, int target, const sylv_tuning *tu, int *b) {
     bool manual = false;
     for (int j = 0; j < p.Nm; ++j) {
         b[j] = 1;
@@ -232,23 +237,36 @@ sylv_status make_sweep(sylv_plan_s &p, const sylv_tuning *tu, std::vector<int> &
             manual = true;
         }
     }
-    if (!manual) {
-        for (;;) {   // balanced doubling of the block with the most blocks left
-            int best = -1;
-            double bestr = 1.0;
-            int64_t prod = 1;
-            for (int j = 0; j < p.Nm; ++j) prod *= b[j];
-            for (int j = 0; j < p.Nm; ++j) {
-                if (b[j] >= p.n[j]) continue;
-                int64_t nb = std::min<int64_t>(2 * b[j], p.n[j]);
-                if (prod / b[j] * nb > target) continue;
-                double r = (double)p.n[j] / b[j];
-                if (r > bestr) { bestr = r; best = j; }
-            }
-            if (best < 0) break;
-            b[best] = (int)std::min<int64_t>(2 * b[best], p.n[best]);
+    if (manual) return;
+    for (;;) {
+        int best = -1;
+        double bestr = 1.0;
+        int64_t prod = 1;
+        for (int j = 0; j < p.Nm; ++j) prod *= b[j];
+        for (int j = 0; j < p.Nm; ++j) {
+            if (b[j] >= p.n[j]) continue;
+            int64_t nb = std::min<int64_t>(2 * b[j], p.n[j]);
+            if (prod / b[j] * nb > target) continue;
+            double r = (double)p.n[j] / b[j];
+            if (r > bestr) { bestr = r; best = j; }
         }
+        if (best < 0) break;
+        b[best] = (int)std::min<int64_t>(2 * b[best], p.n[best]);
     }
+}
+
+int64_t tiles_for(const sylv_plan_s &p, const int *b) {
+    int64_t ts = 1;
+    for (int j = 0; j < p.Nm; ++j) ts *= (p.n[j] + b[j] - 1) / b[j];
+    return ts * p.nrhs;
+}
+
+// Host tables of one sweep configuration (tile extents b, `threads` per CTA),
+// uploaded into a device buffer of its own.
+sylv_status build_sweep(const sylv_plan_s &p, const int *b, int threads, SweepConfig &cfg) {
+    SweepArgs &a = cfg.a;
+    a = SweepArgs{};
+    a.Nm = p.Nm;
     int64_t ts = 1;
     a.nin = 0;
     int bs = 1;
@@ -277,20 +295,19 @@ sylv_status make_sweep(sylv_plan_s &p, const sylv_tuning *tu, std::vector<int> &
     a.ntiles = ts * p.nrhs;
     a.sig_re = p.sigma.real();
     a.sig_im = p.sigma.imag();
-    a.timeout_cycles = 4000000000LL;
+    a.timeout_cycles = p.timeout_cycles;
+    a.fault_tile = p.fault_tile;
 
     // in-tile schedule: box offsets sorted by their distance from the tile end
-    std::vector<int> lvl(a.Pt);
-    std::vector<int> cntl(a.Lin + 1, 0);
+    std::vector<int> lvl(a.Pt), cntl(a.Lin + 1, 0);
     for (int e = 0; e < a.Pt; ++e) {
-        int s = 0;
-        for (int q = 0; q < a.nin; ++q) s += (e / a.BS[q]) % a.b[a.inmode[q]];
-        lvl[e] = s;
-        cntl[s + 1]++;
+        int sum = 0;
+        for (int q = 0; q < a.nin; ++q) sum += (e / a.BS[q]) % a.b[a.inmode[q]];
+        lvl[e] = sum;
+        cntl[sum + 1]++;
     }
-    lev.assign(a.Lin + 1, 0);
+    std::vector<int> lev(a.Lin + 1, 0), sched(a.Pt, 0);
     for (int l = 0; l < a.Lin; ++l) lev[l + 1] = lev[l] + cntl[l + 1];
-    sched.assign(a.Pt, 0);
     {
         std::vector<int> pos(lev.begin(), lev.end() - 1);
         for (int e = 0; e < a.Pt; ++e) sched[pos[lvl[e]]++] = e;
@@ -303,8 +320,8 @@ sylv_status make_sweep(sylv_plan_s &p, const sylv_tuning *tu, std::vector<int> &
         a.bmax = std::max(a.bmax, a.b[a.inmode[q]]);
         if (a.b[a.inmode[q]] > 255) a.fast = 0;
     }
-    sched_e.assign(a.Pt, 0);
-    coord.assign(a.Pt, 0ull);
+    std::vector<int> sched_e(a.Pt, 0);
+    std::vector<unsigned long long> coord(a.Pt, 0ull);
     for (int qq = 0; qq < a.Pt; ++qq) {
         int e = 0;
         for (int q = 0; q < a.nin; ++q) {
@@ -328,10 +345,10 @@ sylv_status make_sweep(sylv_plan_s &p, const sylv_tuning *tu, std::vector<int> &
     std::vector<int> tl((size_t)ts);
     std::vector<int64_t> cnt((size_t)maxlev + 2, 0);
     for (int64_t t = 0; t < ts; ++t) {
-        int s = 0;
-        for (int j = 0; j < p.Nm; ++j) s += a.Bc[j] - 1 - (int)((t / a.TS[j]) % a.Bc[j]);
-        tl[(size_t)t] = s;
-        cnt[(size_t)s + 1]++;
+        int sum = 0;
+        for (int j = 0; j < p.Nm; ++j) sum += a.Bc[j] - 1 - (int)((t / a.TS[j]) % a.Bc[j]);
+        tl[(size_t)t] = sum;
+        cnt[(size_t)sum + 1]++;
     }
     for (int l = 0; l <= maxlev; ++l) cnt[(size_t)l + 1] += cnt[(size_t)l];
     std::vector<int> by_level((size_t)ts);
@@ -339,24 +356,55 @@ sylv_status make_sweep(sylv_plan_s &p, const sylv_tuning *tu, std::vector<int> &
         std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
         for (int64_t t = 0; t < ts; ++t) by_level[(size_t)pos[(size_t)tl[(size_t)t]]++] = (int)t;
     }
-    order.resize((size_t)(ts * p.nrhs));
+    std::vector<int> order((size_t)(ts * p.nrhs));
     size_t w = 0;
     for (int l = 0; l <= maxlev; ++l)
         for (int64_t r = 0; r < p.nrhs; ++r)
             for (int64_t q = cnt[(size_t)l]; q < cnt[(size_t)l + 1]; ++q)
                 order[w++] = (int)(r * ts + by_level[(size_t)q]);
 
-    p.sweep_threads = p.fp64() ? 128 : 256;
-    if (tu && tu->sweep_threads > 0) p.sweep_threads = std::min(256, (tu->sweep_threads + 31) / 32 * 32);
-    // FP64 reciprocals, tile values, one staged block of T
+    // FP64 reciprocals, tile values, one staged block of T, diagonal T blocks
     const size_t esz = p.fp64() ? 16 : 8;
     int td = 0;
     for (int q = 0; q < a.nin; ++q) {
         a.tdoff[q] = td;
         td += a.b[a.inmode[q]] * a.b[a.inmode[q]];
     }
-    p.sweep_smem = (size_t)a.Pt * (esz + 16) + ((size_t)SWEEP_KCH * a.bmax + td) * esz;
-    if (p.sweep_smem > 200 * 1024) return SYLV_ERR_SHAPE;
+    cfg.threads = threads;
+    cfg.smem = (size_t)a.Pt * (esz + 16) + ((size_t)SWEEP_KCH * a.bmax + td) * esz;
+    if (cfg.smem > 200 * 1024) return SYLV_ERR_SHAPE;
+
+    // device tables: order | sched | lev | sched_e | coord
+    size_t o_order = 0;
+    size_t o_sched = align256(o_order + order.size() * 4);
+    size_t o_lev = align256(o_sched + sched.size() * 4);
+    size_t o_se = align256(o_lev + lev.size() * 4);
+    size_t o_coord = align256(o_se + sched_e.size() * 4);
+    size_t total = align256(o_coord + coord.size() * 8);
+    std::vector<unsigned char> host(total, 0);
+    std::memcpy(host.data() + o_order, order.data(), order.size() * 4);
+    std::memcpy(host.data() + o_sched, sched.data(), sched.size() * 4);
+    std::memcpy(host.data() + o_lev, lev.data(), lev.size() * 4);
+    std::memcpy(host.data() + o_se, sched_e.data(), sched_e.size() * 4);
+    std::memcpy(host.data() + o_coord, coord.data(), coord.size() * 8);
+    if (cudaMalloc(&cfg.dbuf, total) != cudaSuccess) {
+        cudaGetLastError();
+        cfg.dbuf = nullptr;
+        return SYLV_ERR_OOM;
+    }
+    if (cudaMemcpy(cfg.dbuf, host.data(), total, cudaMemcpyHostToDevice) != cudaSuccess)
+        return SYLV_ERR_CUDA;
+    unsigned char *base = (unsigned char *)cfg.dbuf;
+    a.order = (const int *)(base + o_order);
+    a.sched = (const int *)(base + o_sched);
+    a.lev_start = (const int *)(base + o_lev);
+    a.sched_e = (const int *)(base + o_se);
+    a.coord = (const unsigned long long *)(base + o_coord);
+
+    // persistent grid: every SM holds as many tiles as fit
+    int per = sweep_blocks_per_sm(p.fp64(), cfg.threads, cfg.smem);
+    if (per < 1) per = 1;
+    cfg.grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)p.num_sms * per, a.ntiles));
     return SYLV_OK;
 }
 
@@ -483,29 +531,27 @@ cudaError_t run_residual(Ctx &c, const void *B, const void *X, void *R, const in
     return cudaSuccess;
 }
 
-cudaError_t run_sweep(Ctx &c, void *Y, bool fp64) {
+cudaError_t run_sweep_cfg(Ctx &c, const SweepConfig &cfg, void *Y, bool fp64) {
     sylv_plan_s *p = c.p;
-    SweepArgs a = p->sw;
+    SweepArgs a = cfg.a;
     a.Y = Y;
     for (int j = 0; j < p->Nm; ++j) {
         a.T[j] = fp64 ? p->T64[j] : p->T32[j];
         a.d[j] = p->d64[j];
     }
-    a.order = p->d_order;
-    a.sched = p->d_sched;
-    a.lev_start = p->d_lev;
-    a.sched_e = p->d_sched_e;
-    a.coord = p->d_coord;
+    a.den_scale = p->den_scale;
     a.cnt = c.cnt;
     a.flags = c.flags;
     cudaError_t e = launch_sweep_init(a, c.st);
     if (e != cudaSuccess) return e;
     count(c);
-    e = launch_sweep(fp64, a, p->sweep_grid, p->sweep_threads, p->sweep_smem, c.st);
+    e = launch_sweep(fp64, a, cfg.grid, cfg.threads, cfg.smem, c.st);
     if (e != cudaSuccess) return e;
     count(c);
     return cudaSuccess;
 }
+
+cudaError_t run_sweep(Ctx &c, void *Y, bool fp64) { return run_sweep_cfg(c, c.p->sweep, Y, fp64); }
 
 sylv_status check_ws(sylv_plan_s *p, void *ws, size_t bytes) {
     if (p->ws_bytes == 0) return SYLV_OK;
@@ -618,6 +664,111 @@ sylv_status solve_impl(sylv_plan_s *p, const void *B, void *X, void *ws, cudaStr
     launches = c.launches;
     p->last_launches = c.launches;
     return SYLV_OK;
+}
+
+// ------------------------------------------------------ batched graphs --
+// One CUDA graph per argument set of sylv_solve_batched: the equations'
+// launch sequences spread round-robin over a fork of up to 8 streams.
+constexpr int BATCH_STREAMS = 8;
+constexpr size_t BATCH_CACHE = 16;
+
+struct BatchGraph {
+    std::vector<const void *> key;
+    std::vector<int> launches;
+    cudaGraphExec_t exec = nullptr;
+};
+
+struct DeviceStreams {
+    cudaStream_t s[BATCH_STREAMS] = {};
+    cudaEvent_t fork = nullptr, join[BATCH_STREAMS] = {};
+    bool ready = false;
+};
+
+std::mutex g_batch_mu;
+std::vector<BatchGraph> g_batch_cache;
+DeviceStreams g_dev_streams[64];
+
+// drop the recorded graphs that reference plan p (its tables changed or died)
+void batch_forget(const void *p) {
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    for (size_t i = 0; i < g_batch_cache.size();) {
+        const auto &k = g_batch_cache[i].key;
+        bool hit = false;
+        for (size_t q = 2; q < k.size(); q += 3) hit |= (k[q] == p);
+        if (hit) {
+            cudaGraphExecDestroy(g_batch_cache[i].exec);
+            g_batch_cache.erase(g_batch_cache.begin() + (long)i);
+        } else {
+            ++i;
+        }
+    }
+}
+
+sylv_status batch_graph_launch(int count, const sylv_plan_t *plans, const void *const *B,
+                               void *const *X, void *ws, cudaStream_t user,
+                               std::vector<int> &launches) {
+    const int dev = plans[0]->device;
+    if (dev < 0 || dev >= 64) return SYLV_ERR_INVALID_ARG;
+    std::vector<const void *> key;
+    key.reserve(3 * (size_t)count + 2);
+    key.push_back(ws);
+    key.push_back(reinterpret_cast<const void *>((uintptr_t)count));
+    for (int e = 0; e < count; ++e) {
+        key.push_back(plans[e]);
+        key.push_back(B[e]);
+        key.push_back(X[e]);
+    }
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    for (auto &g : g_batch_cache)
+        if (g.key == key) {
+            launches = g.launches;
+            return cudaGraphLaunch(g.exec, user) == cudaSuccess ? SYLV_OK : SYLV_ERR_CUDA;
+        }
+    DeviceStreams &ds = g_dev_streams[dev];
+    if (!ds.ready) {
+        for (int k = 0; k < BATCH_STREAMS; ++k)
+            if (cudaStreamCreateWithFlags(&ds.s[k], cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&ds.join[k], cudaEventDisableTiming) != cudaSuccess)
+                return SYLV_ERR_CUDA;
+        if (cudaEventCreateWithFlags(&ds.fork, cudaEventDisableTiming) != cudaSuccess)
+            return SYLV_ERR_CUDA;
+        ds.ready = true;
+    }
+    const int S = std::min(count, BATCH_STREAMS);
+    cudaStream_t cs = ds.s[0];
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return SYLV_ERR_CUDA;
+    bool ok = cudaEventRecord(ds.fork, cs) == cudaSuccess;
+    for (int k = 1; ok && k < S; ++k) ok = cudaStreamWaitEvent(ds.s[k], ds.fork, 0) == cudaSuccess;
+    size_t off = 0;
+    for (int e = 0; ok && e < count; ++e) {
+        ok = solve_impl(plans[e], B[e], X[e], (char *)ws + off, ds.s[e % S],
+                        launches[(size_t)e]) == SYLV_OK;
+        off += align256(plans[e]->ws_bytes);
+    }
+    for (int k = 1; ok && k < S; ++k)
+        ok = cudaEventRecord(ds.join[k], ds.s[k]) == cudaSuccess &&
+             cudaStreamWaitEvent(cs, ds.join[k], 0) == cudaSuccess;
+    cudaGraph_t graph = nullptr;
+    cudaError_t ec = cudaStreamEndCapture(cs, &graph);
+    if (!ok || ec != cudaSuccess || !graph) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return SYLV_ERR_CUDA;
+    }
+    BatchGraph bg;
+    bg.key = std::move(key);
+    bg.launches = launches;
+    ec = cudaGraphInstantiate(&bg.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ec != cudaSuccess) return SYLV_ERR_CUDA;
+    if (g_batch_cache.size() >= BATCH_CACHE) {
+        cudaGraphExecDestroy(g_batch_cache.front().exec);
+        g_batch_cache.erase(g_batch_cache.begin());
+    }
+    g_batch_cache.push_back(std::move(bg));
+    return cudaGraphLaunch(g_batch_cache.back().exec, user) == cudaSuccess ? SYLV_OK
+                                                                           : SYLV_ERR_CUDA;
 }
 
 }  // namespace
@@ -755,6 +906,15 @@ sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t 
     DeviceGuard dg(device);
     if (!dg.ok) return SYLV_ERR_CUDA;
     if (ensure_init(device) != SYLV_OK) return SYLV_ERR_CUDA;
+    {
+        int sms = 0, khz = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+        cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, device);
+        p->num_sms = std::max(1, sms);
+        const long long ms = (tuning && tuning->timeout_ms > 0) ? tuning->timeout_ms : 2000;
+        p->timeout_cycles = ms * (long long)std::max(khz, 1000000);
+        p->fault_tile = (tuning && tuning->fault_tile > 0) ? tuning->fault_tile - 1 : -1;
+    }
 
     // transform and residual passes
     const int gmax = tuning ? tuning->group_max : 0;
@@ -763,11 +923,6 @@ sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t 
     if (s != SYLV_OK) return s;
     s = make_groups(*p, true, false, gmax, false, p->rgroups);
     if (s != SYLV_OK) return s;
-    std::vector<int> order, sched, lev, sched_e;
-    std::vector<unsigned long long> coord;
-    s = make_sweep(*p, tuning, order, sched, lev, sched_e, coord);
-    if (s != SYLV_OK) return s;
-
     // device pool: per mode Uh64 U64 A64 T64 d64 Uh32 U32 T32, then the tables
     size_t off = 0;
     std::vector<size_t> offs;
@@ -778,12 +933,7 @@ sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t 
         reserve((size_t)p->n[j] * 16);
         reserve(nn * 8); reserve(nn * 8); reserve(nn * 8);
     }
-    reserve(order.size() * 4);
-    reserve(sched.size() * 4);
-    reserve(lev.size() * 4);
     reserve(3 * sizeof(unsigned long long));
-    reserve(sched_e.size() * 4);
-    reserve(coord.size() * 8);
     const size_t tc_first = offs.size();
     for (auto &g : p->tgroups)
         if (g.tc) {
@@ -839,19 +989,9 @@ sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t 
         p->T32[j] = base + offs[oi + 7];
         oi += 8;
     }
-    std::memcpy(host.data() + offs[oi], order.data(), order.size() * 4);
-    std::memcpy(host.data() + offs[oi + 1], sched.data(), sched.size() * 4);
-    std::memcpy(host.data() + offs[oi + 2], lev.data(), lev.size() * 4);
-    p->d_order = (int *)(base + offs[oi]);
-    p->d_sched = (int *)(base + offs[oi + 1]);
-    p->d_lev = (int *)(base + offs[oi + 2]);
-    unsigned long long *dm = (unsigned long long *)(base + offs[oi + 3]);
+    unsigned long long *dm = (unsigned long long *)(base + offs[oi]);
     unsigned long long init3[3] = {~0ull, 0ull, 0ull};
-    std::memcpy(host.data() + offs[oi + 3], init3, sizeof(init3));
-    std::memcpy(host.data() + offs[oi + 4], sched_e.data(), sched_e.size() * 4);
-    std::memcpy(host.data() + offs[oi + 5], coord.data(), coord.size() * 8);
-    p->d_sched_e = (int *)(base + offs[oi + 4]);
-    p->d_coord = (unsigned long long *)(base + offs[oi + 5]);
+    std::memcpy(host.data() + offs[oi], init3, sizeof(init3));
     // tensor-core B operands: B[k, i] = Re M[i, k], B[k, n + i] = Im M[i, k]
     // (M = U^* forward, U back), split into TF32 hi and lo, in the K-major
     // no-swizzle layout the kernel's descriptors describe
@@ -905,24 +1045,31 @@ sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t 
     p->max_den = mx;
     if (r3[2] != 0 || !(mn > 0.0) || !std::isfinite(mx)) return SYLV_ERR_SINGULAR;
     // power of two centring |scale * sum|^2 on 1 for the sweep's reciprocals
-    p->sw.den_scale = std::ldexp(1.0, -(int)std::lround(0.5 * (std::log2(mn) + std::log2(mx))));
+    p->den_scale = std::ldexp(1.0, -(int)std::lround(0.5 * (std::log2(mn) + std::log2(mx))));
 
-    // sweep grid: every SM holds as many tiles as fit
+    // sweep: default tiles (FP64 256 entries x 128 threads, FP32 1024 x 256,
+    // measured on GB300) or the caller's block extents
     {
-        int sms = 0;
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-        p->num_sms = std::max(1, sms);
-        int per = sweep_blocks_per_sm(p->fp64(), p->sweep_threads, p->sweep_smem);
-        if (per < 1) per = 1;
-        int64_t grid = (int64_t)sms * per;
-        grid = std::min<int64_t>(grid, p->sw.ntiles);
-        p->sweep_grid = (int)std::max<int64_t>(1, grid);
+        int b[MAXM];
+        choose_blocks(*p, p->fp64() ? 256 : 1024, tuning, b);
+        int threads = p->fp64() ? 128 : 256;
+        if (tuning && tuning->sweep_threads > 0)
+            threads = std::min(256, (tuning->sweep_threads + 31) / 32 * 32);
+        s = build_sweep(*p, b, threads, p->sweep);
+        if (s != SYLV_OK) return s;
+        // tile counters for any tiling the autotuner may install (tiles >= 64 entries)
+        p->cnt_capacity = p->sweep.a.ntiles;
+        for (int target = 64; target <= 4096; target *= 2) {
+            int bt[MAXM];
+            choose_blocks(*p, target, nullptr, bt);
+            p->cnt_capacity = std::max(p->cnt_capacity, tiles_for(*p, bt));
+        }
     }
 
     // workspace layout
     size_t w = align256(sizeof(DevFlags));
     p->off_cnt = w;
-    w = align256(w + (size_t)p->sw.ntiles * 4);
+    w = align256(w + (size_t)p->cnt_capacity * 4);
     if (!p->fp64()) {
         p->off_W = w;
         w = align256(w + (size_t)(p->ntot * p->nrhs) * 8);
@@ -936,6 +1083,7 @@ sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t 
 
 sylv_status sylv_plan_destroy(sylv_plan_t plan) {
     if (!plan) return SYLV_ERR_INVALID_ARG;
+    batch_forget(plan);
     delete plan;
     return SYLV_OK;
 }
@@ -983,20 +1131,33 @@ sylv_status sylv_solve_batched(int count, const sylv_plan_t *plans, const void *
     if (s != SYLV_OK) return s;
     if (need > 0 && (!ws || ws_bytes < need)) return SYLV_ERR_WORKSPACE;
     if (((uintptr_t)ws) & 255) return SYLV_ERR_INVALID_ARG;
+    if (count == 0) return SYLV_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    size_t off = 0;
-    std::vector<int> launches((size_t)count, 0);
+    bool direct = false;
+    const int dev = plans[0]->device;
     for (int e = 0; e < count; ++e) {
         sylv_plan_s *p = plans[e];
         if (!B[e] || !X[e] || (!p->fp64() && B[e] == X[e])) return SYLV_ERR_INVALID_ARG;
-        DeviceGuard dg(p->device);
-        if (!dg.ok) return SYLV_ERR_CUDA;
-        s = solve_impl(p, B[e], X[e], (char *)ws + off, st, launches[(size_t)e]);
+        if ((((uintptr_t)B[e]) | ((uintptr_t)X[e])) & 15) return SYLV_ERR_INVALID_ARG;
+        if (p->timing) direct = true;
+        if (p->device != dev) return SYLV_ERR_INVALID_ARG;
+    }
+    DeviceGuard dg(dev);
+    if (!dg.ok) return SYLV_ERR_CUDA;
+    std::vector<int> launches((size_t)count, 0);
+    if (direct) {
+        size_t off = 0;
+        for (int e = 0; e < count; ++e) {
+            s = solve_impl(plans[e], B[e], X[e], (char *)ws + off, st, launches[(size_t)e]);
+            if (s != SYLV_OK) return s;
+            off += align256(plans[e]->ws_bytes);
+        }
+    } else {
+        s = batch_graph_launch(count, plans, B, X, ws, st, launches);
         if (s != SYLV_OK) return s;
-        off += align256(p->ws_bytes);
     }
     if (infos) {
-        off = 0;
+        size_t off = 0;
         sylv_status worst = SYLV_OK;
         for (int e = 0; e < count; ++e) {
             sylv_status r = fill_info(plans[e], reinterpret_cast<DevFlags *>((char *)ws + off),
@@ -1006,6 +1167,75 @@ sylv_status sylv_solve_batched(int count, const sylv_plan_t *plans, const void *
         }
         return worst;
     }
+    return SYLV_OK;
+}
+
+sylv_status sylv_plan_autotune(sylv_plan_t p, void *Tdev, void *ws, size_t ws_bytes,
+                               void *stream, int32_t *block_out, float *best_ms) {
+    if (!p || !Tdev) return SYLV_ERR_INVALID_ARG;
+    sylv_status s = check_ws(p, ws, ws_bytes);
+    if (s != SYLV_OK) return s;
+    DeviceGuard dg(p->device);
+    if (!dg.ok) return SYLV_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t esz = p->fp64() ? 16 : 8;
+    batch_forget(p);
+    if (cudaMemsetAsync(Tdev, 0, (size_t)(p->ntot * p->nrhs) * esz, st) != cudaSuccess)
+        return SYLV_ERR_CUDA;
+    Ctx c{p, st, reinterpret_cast<DevFlags *>(ws),
+          reinterpret_cast<int *>((char *)ws + p->off_cnt)};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return SYLV_ERR_CUDA;
+    auto time_cfg = [&](const SweepConfig &cfg, float &ms) -> bool {
+        float best = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {          // first run warms up
+            if (launch_solve_init(c.flags, st) != cudaSuccess) return false;
+            if (cudaEventRecord(e0, st) != cudaSuccess) return false;
+            if (run_sweep_cfg(c, cfg, Tdev, p->fp64()) != cudaSuccess) return false;
+            if (cudaEventRecord(e1, st) != cudaSuccess) return false;
+            if (cudaEventSynchronize(e1) != cudaSuccess) return false;
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (rep > 0) best = std::min(best, t);
+        }
+        ms = best;
+        return true;
+    };
+    float cur_ms = 0.f;
+    bool ok = time_cfg(p->sweep, cur_ms);
+    for (int target = 64; ok && target <= 2048; target *= 2) {
+        int b[MAXM];
+        choose_blocks(*p, target, nullptr, b);
+        if (tiles_for(*p, b) > p->cnt_capacity) continue;
+        for (int threads = 128; threads <= 256; threads *= 2) {
+            SweepConfig cand;
+            if (build_sweep(*p, b, threads, cand) != SYLV_OK) {
+                if (cand.dbuf) cudaFree(cand.dbuf);
+                continue;
+            }
+            float ms = 0.f;
+            if (!time_cfg(cand, ms)) {
+                ok = false;
+                cudaFree(cand.dbuf);
+                break;
+            }
+            if (ms < cur_ms) {
+                cudaFree(p->sweep.dbuf);
+                p->sweep = cand;
+                cur_ms = ms;
+            } else {
+                cudaFree(cand.dbuf);
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!ok) return SYLV_ERR_CUDA;
+    if (block_out)
+        for (int j = 0, q = 0; j < p->N_in; ++j)
+            block_out[j] = (q < p->Nm && p->orig[q] == j) ? p->sweep.a.b[q++] : 1;
+    if (best_ms) *best_ms = cur_ms;
     return SYLV_OK;
 }
 
@@ -1139,7 +1369,7 @@ sylv_status static_scratch(int dev, void **out) {
 extern "C" sylv_status sylv_sweep_static(sylv_plan_t p, void *Tdev, void *stream) {
     if (!p || !Tdev) return SYLV_ERR_INVALID_ARG;
     const size_t cnt_off = align256(sizeof(DevFlags));
-    if (cnt_off + align256((size_t)p->sw.ntiles * 4) > SYLV_STATIC_SCRATCH_BYTES)
+    if (cnt_off + align256((size_t)p->sweep.a.ntiles * 4) > SYLV_STATIC_SCRATCH_BYTES)
         return SYLV_ERR_SHAPE;
     DeviceGuard dg(p->device);
     if (!dg.ok) return SYLV_ERR_CUDA;

@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(256) k_sweep(const __grid_constant__ SweepArgs
         }
         __threadfence();
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == 0 && tile != a.fault_tile) {
             for (int j = 0; j < Nm; ++j)
                 if (s_I[j] > 0) atomicSub(a.cnt + tile - a.TS[j], 1);
         }

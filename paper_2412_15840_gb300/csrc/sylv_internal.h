@@ -90,6 +90,7 @@ struct SweepArgs {
     const unsigned long long *coord;  // per box offset: in-tile coordinates, 8 bits each
     const int *lev_start;     // Lin + 1 entries
     long long timeout_cycles;
+    int fault_tile;           // test hook: this tile never releases its predecessors (-1: none)
 };
 
 // Tensor-core (tcgen05, 3xTF32) transform pass over one mode, complex64 in.
