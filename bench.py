@@ -61,6 +61,10 @@ def parse():
                     help="skip the oracle error check and CPU baseline")
     ap.add_argument("--kernels-once", action="store_true",
                     help="run each hot-path kernel family once on the workload (for ncu)")
+    ap.add_argument("--workload", default="n64_N4",
+                    choices=["n64_N4", "batch512", "advdiff48", "n2_N29", "n19_N7"],
+                    help="n64_N4 is the benchmark line; the others measure the other "
+                         "synthetic workloads (one JSON line each)")
     return ap.parse_args()
 
 
@@ -166,6 +170,119 @@ def config_block():
 
 # ------------------------------------------------------------------- ours --
 
+def sampled_eta(A, B_flat, X_dev, shape, nrhs, count=1000, seed=11):
+    """Backward error at sampled entries: r_i = b_i - sum_j sum_k a_{j,i_j k} x_{..k..},
+    eta = max|r_i| / (sum_j ||A_j||_inf ||X||_inf + ||B||_inf)  (host arithmetic)."""
+    import torch
+    rng = np.random.default_rng(seed)
+    N = len(shape)
+    S = np.cumprod((1,) + tuple(shape[:-1]), dtype=np.int64)
+    ntot = int(np.prod(shape, dtype=np.int64))
+    ii = np.stack([rng.integers(0, shape[j], size=count) for j in range(N)], axis=1)
+    lin = (ii * S).sum(axis=1) + rng.integers(0, nrhs, size=count) * ntot
+    acc = np.zeros(count, dtype=np.complex128)
+    for j in range(N):
+        idx = lin[:, None] + (np.arange(shape[j])[None, :] - ii[:, j:j + 1]) * S[j]
+        xs = X_dev[torch.as_tensor(idx.reshape(-1), device=X_dev.device)].cpu().numpy()
+        acc += np.einsum("ck,ck->c", A[j][ii[:, j], :], xs.reshape(count, shape[j]))
+    r = B_flat[lin] - acc
+    an = sum(float(np.abs(a).sum(axis=1).max()) for a in A)
+    return float(np.abs(r).max()) / (an * float(X_dev.abs().max().item()) + float(np.abs(B_flat).max()))
+
+
+def other_workload(args, local: int) -> int:
+    """One JSON line for a non-default synthetic workload (both precisions)."""
+    import torch
+    from paper_2412_15840_gb300.build import build
+    build()
+    from paper_2412_15840_gb300 import (Plan, from_device, solve_batched, to_device,
+                                        workspace_size_batched)
+    import oracle
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    import torch.distributed as dist
+    from paper_2412_15840_gb300.dist import max_over_ranks, shard, sum_over_ranks
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl", device_id=dev)
+    name = args.workload
+    if name == "batch512":
+        probs = si.uneven_batch(512, 4, seed=0)
+        desc = "512 N=3 equations, n_k ~ U{16..96} (seed 0), A=(randn+i randn)/sqrt(n)+3I, 4 RHS"
+    elif name == "advdiff48":
+        probs = [si.advdiff_n48()]
+        desc = "N=3, n=48 periodic advection-diffusion (0.01 D2 + 0.5 D1 + I), 32 RHS"
+    elif name == "n2_N29":
+        probs = [si.binary_N29()]
+        desc = "N=29, n=2 (modes 5, 17 singletons [1.5]), 2x2 (randn+i randn)/sqrt(2)+2I, 2^27"
+    else:
+        probs = [si.cube_n19_N7()]
+        desc = "N=7, n=19 (893,871,739 entries), A=(randn+i randn)/sqrt(19)+3I"
+    if name == "batch512" and world > 1:
+        # independent equations: each rank solves its share, no data-path collective
+        mine = shard([float(p.n_tot * p.nrhs) for p in probs], rank, world)
+        probs = [probs[e] for e in mine]
+    # other workloads: one equation does not split across GPUs, every rank
+    # solves its own replica
+    entries_local = sum(p.n_tot * p.nrhs for p in probs)
+    entries = int(sum_over_ranks(entries_local, device=dev))
+    Bs = [to_device(p.B, device=dev) for p in probs]
+    out = {"workload": name, "description": desc, "entries": entries, "equations": len(probs)}
+    stream = torch.cuda.current_stream(dev)
+    for prec in ("mixed", "fp64"):
+        t0 = time.perf_counter()
+        plans = [Plan(A=p.A, nrhs=p.nrhs, prec=prec, rtol=RTOL, max_refine=MAX_REFINE,
+                      device=local) for p in probs]
+        setup = time.perf_counter() - t0
+        Xs = [torch.empty_like(b) for b in Bs]
+        ws = torch.empty(max(256, workspace_size_batched(plans)), dtype=torch.uint8, device=dev)
+
+        def step():
+            solve_batched(plans, Bs, Xs, ws, stream=stream)
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, device=dev)
+        infos = solve_batched(plans, Bs, Xs, ws, stream=stream, info=True)
+        rec = {"ms_per_step": ms, "value": entries / (ms * 1e-3), "setup_s": setup,
+               "max_refine_iters": max(i["refine_iters"] for i in infos),
+               "status": sorted({i["status"] for i in infos})}
+        if name in ("batch512", "advdiff48"):
+            pick = [min(range(len(probs)), key=lambda e: probs[e].n_tot)] if name == "batch512" \
+                else [0]
+            if name == "batch512":
+                pick += [1, 2]
+            rec["rel_err_vs_oracle_max"] = max(
+                oracle.rel_err(from_device(Xs[e], probs[e].B.shape),
+                               oracle.solve(probs[e].A, probs[e].B)) for e in pick)
+            rec["oracle_checked_equations"] = pick
+        else:
+            p = probs[0]
+            rec["sampled_backward_error"] = sampled_eta(p.A, p.B.reshape(-1, order="F"), Xs[0],
+                                                        p.shape, p.nrhs)
+        out[prec] = rec
+        del plans, Xs, ws
+        torch.cuda.empty_cache()
+    line = {"metric": METRIC, "unit": UNIT, "value": out["mixed"]["value"], "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak" if name == "batch512" else "replicas only",
+            "data": "synthetic", "config": out}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def kernels_once(local: int) -> int:
     """One launch group of every hot-path kernel family, in this order:
     FP64 residual passes, FP32 forward passes, FP32 sweep, FP64 forward
@@ -202,6 +319,8 @@ def main():
         return run_reference(args, rank, world)
     if args.kernels_once:
         return kernels_once(local)
+    if args.workload != "n64_N4":
+        return other_workload(args, local)
 
     import torch
     import torch.distributed as dist
@@ -220,12 +339,10 @@ def main():
         if world > 1:
             dist.barrier()
 
+    from paper_2412_15840_gb300.dist import max_over_ranks as _mor
+
     def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return _mor(x, device=dev)
 
     p = si.random_problem(SHAPE, 1, seed=rank, name="N4_n64")
     entries = p.n_tot * p.nrhs
