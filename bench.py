@@ -43,7 +43,8 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
 # DRAM traffic per launch of the FP64 residual pass kernel, from an ncu capture
 # (see profiles/); valid only for the kernel source it was measured on.
-TRAFFIC = {"kernels_sha": None, "bytes_per_launch": None}
+TRAFFIC = {"kernels_sha": "eb938f11ee2da734", "bytes_per_launch": 759.5e6,
+           "source": "profiles/kernels_N4_n64.md (mean of the 4 residual-pass launches)"}
 
 
 def kernels_sha() -> str:
@@ -453,7 +454,8 @@ def main():
         "roofline": {"bound": "alu", "kernel": "k_modeprod<double,...,EPI_RESID> (FP64 residual)",
                      "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
-                     "traffic": traffic,
+                     "traffic": traffic, "traffic_unit": "bytes per launch",
+                     "algorithmic_bytes_per_launch": 3 * nbytes,
                      "peak_note": "FP64 FMA pipe derived: 152 SMs x 2 FMA/clk x 2 FLOP x 2070 MHz"},
         "phases_ms_per_solve": {
             "mixed": {k: v / solves for k, v in phases_m["ms"].items()},
