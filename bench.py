@@ -63,7 +63,8 @@ def parse():
     ap.add_argument("--kernels-once", action="store_true",
                     help="run each hot-path kernel family once on the workload (for ncu)")
     ap.add_argument("--workload", default="n64_N4",
-                    choices=["n64_N4", "batch512", "advdiff48", "n2_N29", "n19_N7"],
+                    choices=["n64_N4", "batch512", "advdiff48", "n2_N29", "n19_N7",
+                             "evolve_n64_N4"],
                     help="n64_N4 is the benchmark line; the others measure the other "
                          "synthetic workloads (one JSON line each)")
     return ap.parse_args()
@@ -284,6 +285,71 @@ def other_workload(args, local: int) -> int:
     return 0
 
 
+def evolve_workload(args, local: int) -> int:
+    """Theorem 1 on the N=4, n=64 operators: X(t) at t = 0.1 of
+    X_t = sum_j A_j (x)_j X + B from a Gaussian X(0), both precisions."""
+    import torch
+    from paper_2412_15840_gb300.build import build
+    build()
+    from paper_2412_15840_gb300 import Plan, from_device, to_device
+    import oracle
+    from paper_2412_15840_gb300.dist import max_over_ranks
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    import torch.distributed as dist
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl", device_id=dev)
+    p = si.cube_n64_N4()
+    X0 = si.initial_state(p.shape, 1, seed=1)
+    t = 0.1
+    Bd, X0d = to_device(p.B, device=dev), to_device(X0, device=dev)
+    entries = p.n_tot * world
+    out = {"workload": "evolve_n64_N4",
+           "description": "Theorem 1: X(0.1) of X_t = sum_j A_j (x)_j X + B, N=4, n_k=64, "
+                          "A=(randn+i randn)/8+3I, B and X(0) unit complex Gaussian",
+           "entries": entries, "t": t}
+    ref = None if args.no_oracle else oracle.evolve(p.A, p.B, X0, t)
+    stream = torch.cuda.current_stream(dev)
+    for prec in ("mixed", "fp64"):
+        plan = Plan(A=p.A, nrhs=1, prec=prec, rtol=RTOL, max_refine=MAX_REFINE, device=local)
+        X = torch.empty_like(Bd)
+        ws = torch.empty(plan.evolve_workspace_bytes(), dtype=torch.uint8, device=dev)
+        plan.set_timing(True)
+        for _ in range(args.warmup):
+            plan.evolve(t, Bd, X0d, X=X, workspace=ws, stream=stream)
+        torch.cuda.synchronize(dev)
+        plan.timing(reset=True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            plan.evolve(t, Bd, X0d, X=X, workspace=ws, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, device=dev)
+        tm = plan.timing(reset=True)
+        _, info = plan.evolve(t, Bd, X0d, X=X, workspace=ws, stream=stream, info=True)
+        rec = {"ms_per_step": ms, "value": entries / (ms * 1e-3),
+               "phase_ms": {k: v / max(1, tm["solves"]) for k, v in tm["ms"].items()},
+               "refine_iters": info["refine_iters"], "status": info["status"]}
+        if ref is not None:
+            rec["rel_err_vs_oracle"] = oracle.rel_err(from_device(X, p.B.shape), ref)
+        out[prec] = rec
+        del plan, X, ws
+        torch.cuda.empty_cache()
+    line = {"metric": "entries evolved/s (Theorem 1, t = 0.1)", "unit": "entries/s",
+            "value": out["mixed"]["value"], "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "replicas only",
+            "data": "synthetic", "config": out}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def kernels_once(local: int) -> int:
     """One launch group of every hot-path kernel family, in this order:
     FP64 residual passes, FP32 forward passes, FP32 sweep, FP64 forward
@@ -320,6 +386,8 @@ def main():
         return run_reference(args, rank, world)
     if args.kernels_once:
         return kernels_once(local)
+    if args.workload == "evolve_n64_N4":
+        return evolve_workload(args, local)
     if args.workload != "n64_N4":
         return other_workload(args, local)
 

@@ -17,7 +17,7 @@
  *    complex64 = 2 floats.
  *  - Matrices (A_j, U_j, T_j) are column-major n_j x n_j complex128 in HOST
  *    memory: entry (a, b) is at [2*(a + b*n_j)].
- *  - Tensors are column-major with i_1 fastest (Section 3, Eq. (index)) and
+ *  - Tensors are column-major with i_1 fastest (Section 2.2, Eq. (index)) and
  *    live in DEVICE memory; a tensor with nrhs right-hand sides has one extra
  *    trailing index of extent nrhs (the right-hand sides are independent).
  *  - Modes with n_j = 1 ("singletons", Section 4) carry a scalar A_j; they are
@@ -71,7 +71,8 @@ typedef struct {
     int32_t status;           /* sylv_status of the device-side checks              */
     int32_t refine_iters;     /* refinement steps taken (0 for SYLV_FP64)             */
     int32_t launches;         /* kernels this call enqueued                           */
-    int32_t reserved;
+    int32_t path;             /* bit 0: the sweep ran as the entrywise division of
+                                 Remark 1 (every A_j normal, see sylv_tuning)          */
     double last_corr_rel;     /* ||D_k|| / ||X_k|| of the last refinement step        */
     double est_rel_err;       /* contraction-based estimate of the final error        */
     double min_abs_den;       /* min |sum_j t_{j,i_j i_j}| over all multi-indices      */
@@ -80,13 +81,14 @@ typedef struct {
 
 /* Phase timing accumulated by CUDA events when enabled with sylv_plan_set_timing. */
 typedef struct {
-    double ms[6];             /* forward, sweep, back, residual, update, total        */
-    int64_t launches[6];      /* kernel launches per phase                             */
+    double ms[8];             /* forward, sweep, back, residual, update, total,
+                                 evolve (the right-hand side of Theorem 1), unused    */
+    int64_t launches[8];      /* kernel launches per phase                             */
     int64_t solves;           /* solves accumulated                                    */
 } sylv_timing;
 
 enum { SYLV_PH_FORWARD = 0, SYLV_PH_SWEEP = 1, SYLV_PH_BACK = 2, SYLV_PH_RESIDUAL = 3,
-       SYLV_PH_UPDATE = 4, SYLV_PH_TOTAL = 5 };
+       SYLV_PH_UPDATE = 4, SYLV_PH_TOTAL = 5, SYLV_PH_EVOLVE = 6 };
 
 /* Optional tuning (NULL = defaults).  block[j] = sweep tile extent along input
  * mode j (0 = automatic); group_max = largest product of adjacent mode sizes
@@ -100,7 +102,14 @@ typedef struct {
     int32_t fault_tile;       /* test hook: k > 0 makes the sweep never release the
                                  predecessors of its (k-1)-th tile, so that their waits
                                  run out and the solve reports SYLV_ERR_TIMEOUT */
-    int32_t reserved[3];
+    int32_t general_sweep;    /* 0 = automatic: when every T_j is diagonal to rounding,
+                                 ||strict upper part of T_j||_F <= 4 n_j 2^-53 ||T_j||_F
+                                 (A_j normal, Section 2, Remark 1), the sweep is the
+                                 entrywise division y = c / (sum_j t_{j,i_j i_j}) of
+                                 Eq. (yi1i2iNdiag), computed in FP64 and ignoring the
+                                 rounding-level off-diagonal entries; 1 = always run
+                                 the triangular sweep of Eq. (yi1i2iN) */
+    int32_t reserved[2];
 } sylv_tuning;
 
 /*
@@ -166,6 +175,35 @@ sylv_status sylv_workspace_size_batched(int count, const sylv_plan_t *plans, siz
 sylv_status sylv_solve_batched(int count, const sylv_plan_t *plans, const void *const *B_dev,
                                void *const *X_dev, void *workspace, size_t workspace_bytes,
                                void *stream, sylv_info *infos);
+
+/*
+ * sylv_evolve -- Theorem 1 (Section 3): the solution at time t of the linear
+ * ODE system
+ *     X_t = sum_j A_j (x)_j X + B,   X(0) = X0,
+ * with the plan's A_j, as the solution of the Sylvester equation
+ *     sum_j A_j (x)_j X(t) = F,
+ *     F = exp(t A_N) (x)_N ( ... exp(t A_1) (x)_1 (sum_j A_j (x)_j X0 + B)) - B
+ * (Eqs. (sylvesterNDC) and (C)).  A singleton mode contributes the scalar
+ * factor exp(t a_j).  F is formed on the device in FP64 (one FP64 pass of the
+ * products A_j (x)_j X0 and one of the exp(t A_j) products), then solved as by
+ * sylv_solve in the plan's precision (with refinement for SYLV_MIXED_FP32).
+ *   t        finite real time (t = 0 returns X0 up to rounding).
+ *   B, X0    device complex128 tensors of the plan's shape (x nrhs), read only.
+ *   X        device complex128 output; may be the same buffer as X0 or B.
+ *   workspace  device buffer of sylv_evolve_workspace_size bytes (256-byte
+ *            aligned): the plan's solve workspace plus one complex128 tensor.
+ *   info     as for sylv_solve (the launches include the F passes).
+ * The exponentials exp(t A_j) are computed on the host (sylv_expm) when t
+ * differs from the previous call's and copied to the plan's device buffers in
+ * stream order; calls with the same t enqueue device work only.
+ * Errors: SYLV_ERR_INVALID_ARG (NULL or misaligned pointers, non-finite t,
+ * non-finite exponentials), SYLV_ERR_WORKSPACE, SYLV_ERR_CUDA, and those of
+ * sylv_solve.
+ */
+sylv_status sylv_evolve_workspace_size(sylv_plan_t plan, size_t *bytes);
+sylv_status sylv_evolve(sylv_plan_t plan, double t, const void *B, const void *X0, void *X,
+                        void *workspace, size_t workspace_bytes, void *stream,
+                        sylv_info *info);
 
 /*
  * Single phases (same tensors and workspace rules as sylv_solve), in the
@@ -246,6 +284,15 @@ sylv_status sylv_plan_timing(sylv_plan_t plan, sylv_timing *out, int reset);
  * textbook one, e.g. Golub & Van Loan, ch. 7).  A, Q, T column-major.
  */
 sylv_status sylv_schur(int64_t n, const double *A, double *Q, double *T);
+
+/*
+ * sylv_expm -- host-only matrix exponential E = exp(M) of an n x n complex128
+ * matrix (column-major, 1 <= n <= 1024), by scaling and squaring with the
+ * [13/13] Pade approximant (Higham, SIAM J. Matrix Anal. Appl. 26(4), 2005).
+ * sylv_evolve uses it for the exp(t A_j) of Eq. (C).  No device is touched.
+ * SYLV_ERR_INVALID_ARG for non-finite input or result.
+ */
+sylv_status sylv_expm(int64_t n, const double *M, double *E);
 
 /* Human-readable name of a status code (static storage). */
 const char *sylv_status_string(sylv_status s);

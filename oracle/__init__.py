@@ -6,11 +6,15 @@ Bartels-Stewart method (Cuesta & de la Hoz, arXiv 2412.15840).  Only the tests,
 import it.  The CUDA library shares no code with it and never calls it.
 
 Pinned by the `-m "not gpu"` tests in tests/test_oracle.py against: the
-worked index example of Section 3 (golden fixture), a dense solve of the
+worked index example of Section 2.2 (golden fixture), a dense solve of the
 Kronecker-sum system of Eq. (systvec), the classical 2-D Sylvester solver
 (Eq. (sylvester)), the FFT closed form for circulant operators and the
 diagonal closed form (Remark 1), the singleton reduction, the residual
-invariant, the nested-loop Algorithm 1, and planted mistakes.
+invariant, the nested-loop Algorithm 1, and planted mistakes.  The ODE solution of
+Theorem 1 (`evolve`) is pinned against the exponential of the augmented
+Kronecker-sum matrix, the scalar closed form for diagonal operators, a
+fourth-order Runge-Kutta integration (the experiment of Section 5.2), its
+t = 0 and steady-state limits, and planted mistakes.
 """
 from .bartels_stewart import (  # noqa: F401
     linear_index,
@@ -25,6 +29,8 @@ from .bartels_stewart import (  # noqa: F401
     back_transform,
     solve,
     solve_with_factors,
+    evolve,
+    evolve_rhs,
     rel_err,
     backward_error,
 )

@@ -47,7 +47,7 @@ def _lib():
 
 
 # ----------------------------------------------------------------------------
-# Index conventions (Section 3, Eq. (index) and Algorithm 2)
+# Index conventions (Section 2.2, Eq. (index) and Algorithm 2)
 # ----------------------------------------------------------------------------
 
 def linear_index(ii: Sequence[int], n: Sequence[int]) -> int:
@@ -223,6 +223,28 @@ def solve(A: Sequence[np.ndarray], B: np.ndarray, timings: Optional[dict] = None
     if timings is not None:
         timings["setup"] = timings.get("setup", 0.0) + (time.perf_counter() - t0)
     return solve_with_factors(factors, B, timings=timings)
+
+
+# ----------------------------------------------------------------------------
+# Theorem 1 (Section 3): the linear ODE X_t = sum_j A_j (x)_j X + B
+# ----------------------------------------------------------------------------
+
+def evolve_rhs(A: Sequence[np.ndarray], B: np.ndarray, X0: np.ndarray, t: float) -> np.ndarray:
+    """F of Eq. (C): exp(t A_N) (x)_N ( ... exp(t A_1) (x)_1 (sum_j A_j (x)_j X0 + B)) - B.
+
+    The matrix exponentials are scipy's (a library primitive); the mode
+    products are applied in the order 1..N written in Eq. (C)."""
+    W = apply_operator(A, X0) + B
+    for j, a in enumerate(A):
+        W = mode_product(scipy.linalg.expm(t * np.asarray(a, dtype=np.complex128)), W, j)
+    return W - B
+
+
+def evolve(A: Sequence[np.ndarray], B: np.ndarray, X0: np.ndarray, t: float) -> np.ndarray:
+    """X(t) of X_t = sum_j A_j (x)_j X + B, X(0) = X0 (Theorem 1): the solution of
+    the Sylvester equation sum_j A_j (x)_j X(t) = F, Eq. (sylvesterNDC)-(C), by
+    Algorithm 3."""
+    return solve(A, evolve_rhs(A, B, X0, t))
 
 
 # ----------------------------------------------------------------------------

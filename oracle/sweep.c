@@ -17,7 +17,7 @@
  * ascending.  Y overwrites C in place because c_i is read once, before y_i is
  * written (remark after Algorithm 2).
  *
- * Layout (Section 3, Eq. (index)): column-major, zero-based
+ * Layout (Section 2.2, Eq. (index)): column-major, zero-based
  * index = sum_j i_j * S_j with S_1 = 1, S_{j+1} = S_j * n_j; the entry that
  * differs only in mode j (i_j -> k) sits at index + (k - i_j) * S_j.
  * Complex numbers are interleaved (re, im) doubles; T_j is column-major, so

@@ -4,7 +4,8 @@
 
 by the non-recursive Bartels-Stewart method (forward transform by the Schur
 factors, triangular sweep, back transform), with a plain FP64 path and an
-FP32 path refined to FP64 accuracy by FP64 residuals.  The compute runs in
+FP32 path refined to FP64 accuracy by FP64 residuals, and the solution at
+any time t of the linear ODE X_t = sum_j A_j (x)_j X + B (Theorem 1).  The compute runs in
 libsylv.so (C ABI in include/sylv.h); this package only marshals arguments.
 """
 from .binding import (  # noqa: F401
@@ -12,6 +13,7 @@ from .binding import (  # noqa: F401
     PHASES,
     Plan,
     SylvError,
+    expm,
     from_device,
     lib,
     schur,
@@ -20,5 +22,5 @@ from .binding import (  # noqa: F401
     workspace_size_batched,
 )
 
-__all__ = ["Plan", "SylvError", "schur", "solve_batched", "workspace_size_batched",
+__all__ = ["Plan", "SylvError", "schur", "expm", "solve_batched", "workspace_size_batched",
            "to_device", "from_device", "lib", "EXPORTED", "PHASES"]

@@ -22,7 +22,7 @@ SYLV_FP64 = 0
 SYLV_MIXED_FP32 = 1
 PRECISIONS = {"fp64": SYLV_FP64, "mixed": SYLV_MIXED_FP32, "mixed_fp32": SYLV_MIXED_FP32}
 
-PHASES = ("forward", "sweep", "back", "residual", "update", "total")
+PHASES = ("forward", "sweep", "back", "residual", "update", "total", "evolve")
 
 STATUS = {0: "SYLV_OK", 1: "SYLV_ERR_INVALID_ARG", 2: "SYLV_ERR_SHAPE", 3: "SYLV_ERR_SINGULAR",
           4: "SYLV_ERR_NOT_CONVERGED", 5: "SYLV_ERR_TIMEOUT", 6: "SYLV_ERR_OOM",
@@ -32,7 +32,8 @@ EXPORTED = ("sylv_plan_create", "sylv_plan_destroy", "sylv_workspace_size", "syl
             "sylv_workspace_size_batched", "sylv_solve_batched", "sylv_forward", "sylv_sweep",
             "sylv_back", "sylv_residual", "sylv_plan_factors", "sylv_plan_set_timing",
             "sylv_plan_timing", "sylv_schur", "sylv_status_string", "sylv_version",
-            "sylv_sweep_static", "sylv_plan_autotune")
+            "sylv_sweep_static", "sylv_plan_autotune", "sylv_evolve_workspace_size",
+            "sylv_evolve", "sylv_expm")
 
 
 class SylvError(RuntimeError):
@@ -44,16 +45,18 @@ class SylvError(RuntimeError):
 
 class Info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("refine_iters", ctypes.c_int32),
-                ("launches", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("launches", ctypes.c_int32), ("path", ctypes.c_int32),
                 ("last_corr_rel", ctypes.c_double), ("est_rel_err", ctypes.c_double),
                 ("min_abs_den", ctypes.c_double), ("max_abs_den", ctypes.c_double)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["diagonal_sweep"] = bool(self.path & 1)
+        return d
 
 
 class Timing(ctypes.Structure):
-    _fields_ = [("ms", ctypes.c_double * 6), ("launches", ctypes.c_int64 * 6),
+    _fields_ = [("ms", ctypes.c_double * 8), ("launches", ctypes.c_int64 * 8),
                 ("solves", ctypes.c_int64)]
 
 
@@ -61,7 +64,7 @@ class Tuning(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int32 * 64), ("group_max", ctypes.c_int32),
                 ("sweep_threads", ctypes.c_int32), ("no_tensor_cores", ctypes.c_int32),
                 ("timeout_ms", ctypes.c_int32), ("fault_tile", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("general_sweep", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 _LIB = None
@@ -114,6 +117,13 @@ def _lib():
         L.sylv_plan_timing.argtypes = [vp, ctypes.POINTER(Timing), ctypes.c_int]
         L.sylv_schur.restype = st
         L.sylv_schur.argtypes = [ctypes.c_int64, vp, vp, vp]
+        L.sylv_expm.restype = st
+        L.sylv_expm.argtypes = [ctypes.c_int64, vp, vp]
+        L.sylv_evolve_workspace_size.restype = st
+        L.sylv_evolve_workspace_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+        L.sylv_evolve.restype = st
+        L.sylv_evolve.argtypes = [vp, ctypes.c_double, vp, vp, vp, vp, ctypes.c_size_t, vp,
+                                  ctypes.POINTER(Info)]
         L.sylv_status_string.restype = ctypes.c_char_p
         L.sylv_status_string.argtypes = [ctypes.c_int]
         L.sylv_version.restype = ctypes.c_int
@@ -147,6 +157,15 @@ def schur(A) -> tuple:
     T = np.zeros((n, n), dtype=np.complex128, order="F")
     _check(_lib().sylv_schur(n, a.ctypes.data, Q.ctypes.data, T.ctypes.data), "sylv_schur")
     return Q, T
+
+
+def expm(M) -> np.ndarray:
+    """Host matrix exponential computed by the library (no GPU needed)."""
+    m = _cmat(M)
+    n = m.shape[0]
+    E = np.zeros((n, n), dtype=np.complex128, order="F")
+    _check(_lib().sylv_expm(n, m.ctypes.data, E.ctypes.data), "sylv_expm")
+    return E
 
 
 def _stream_handle(stream) -> Optional[int]:
@@ -185,7 +204,7 @@ class Plan:
                  rtol: float = 1e-10, max_refine: int = 5, device: int = 0,
                  block: Optional[Sequence[int]] = None, group_max: int = 0,
                  sweep_threads: int = 0, tensor_cores: bool = True, timeout_ms: int = 0,
-                 fault_tile: int = 0):
+                 fault_tile: int = 0, general_sweep: bool = False):
         L = _lib()
         if (A is None) == (Q is None or T is None):
             raise ValueError("give A, or both Q and T")
@@ -208,7 +227,7 @@ class Plan:
         pT = ptrs(T) if T is not None else None
         tun = None
         if block is not None or group_max or sweep_threads or not tensor_cores or timeout_ms \
-                or fault_tile:
+                or fault_tile or general_sweep:
             tun = Tuning()
             if block is not None:
                 for j, b in enumerate(block):
@@ -218,6 +237,7 @@ class Plan:
             tun.no_tensor_cores = 0 if tensor_cores else 1
             tun.timeout_ms = int(timeout_ms)
             tun.fault_tile = int(fault_tile)
+            tun.general_sweep = int(bool(general_sweep))
         h = vp()
         s = L.sylv_plan_create(ctypes.byref(h), self.N, n, self.nrhs, pA, pQ, pT, self.prec,
                                float(rtol), int(max_refine), int(device),
@@ -265,6 +285,35 @@ class Plan:
                 _check(s, "sylv_solve")
             return X, inf.as_dict()
         _check(s, "sylv_solve")
+        return X
+
+    def evolve_workspace_bytes(self) -> int:
+        sz = ctypes.c_size_t()
+        _check(_lib().sylv_evolve_workspace_size(self._h, ctypes.byref(sz)),
+               "sylv_evolve_workspace_size")
+        return int(sz.value)
+
+    def evolve(self, t: float, B, X0, X=None, workspace=None, stream=None, info: bool = False):
+        """X(t) of X_t = sum_j A_j (x)_j X + B, X(0) = X0 (Theorem 1); flat complex128
+        device tensors.  `workspace` holds at least evolve_workspace_bytes()."""
+        import torch
+        for v in (B, X0):
+            if v.dtype != torch.complex128 or v.numel() != self.numel:
+                raise ValueError("B and X0 must be complex128 with prod(shape)*nrhs elements")
+        if X is None:
+            X = torch.empty_like(B)
+        if workspace is None:
+            workspace = torch.empty(self.evolve_workspace_bytes(), dtype=torch.uint8,
+                                    device=f"cuda:{self.device}")
+        inf = Info() if info else None
+        s = _lib().sylv_evolve(self._h, float(t), _ptr(B), _ptr(X0), _ptr(X),
+                               workspace.data_ptr(), workspace.numel(), _stream_handle(stream),
+                               ctypes.byref(inf) if inf is not None else None)
+        if info:
+            if s not in (0, 4):
+                _check(s, "sylv_evolve")
+            return X, inf.as_dict()
+        _check(s, "sylv_evolve")
         return X
 
     def forward(self, Tns, workspace=None, stream=None):
@@ -328,8 +377,8 @@ class Plan:
     def timing(self, reset: bool = True) -> dict:
         t = Timing()
         _check(_lib().sylv_plan_timing(self._h, ctypes.byref(t), int(reset)), "sylv_plan_timing")
-        return {"ms": {PHASES[i]: t.ms[i] for i in range(6)},
-                "launches": {PHASES[i]: int(t.launches[i]) for i in range(6)},
+        return {"ms": {PHASES[i]: t.ms[i] for i in range(len(PHASES))},
+                "launches": {PHASES[i]: int(t.launches[i]) for i in range(len(PHASES))},
                 "solves": int(t.solves)}
 
     def close(self):

@@ -125,6 +125,19 @@ struct sylv_plan_s {
     long long timeout_cycles = 4000000000LL;   // per dependency wait
     int fault_tile = -1;                       // test hook (sylv_tuning.fault_tile - 1)
 
+    // Theorem 1 (sylv_evolve): FP64 composition passes with exp(t A_j), the
+    // negated A_j for the first step of Eq. (C), and the last t prepared
+    std::vector<Group> egroups;
+    const void *nA64[MAXM] = {}, *E64[MAXM] = {};
+    std::vector<double> Ehost;
+    double evolve_t = 0.0;
+    bool evolve_ready = false;
+    cd evolve_eps = 1.0;          // exp(t * sigma): the singleton modes' exponentials
+
+    // Remark 1: every T_j diagonal to rounding -> entrywise-division sweep
+    bool diag_sweep = false;
+    DiagArgs diag{};
+
     double min_den = 0.0, max_den = 0.0;
     size_t off_cnt = 0, off_W = 0, off_R = 0, ws_bytes = 0;
 
@@ -244,8 +257,8 @@ void choose_blocks(const sylv_plan_s &p, int target, const sylv_tuning *tu, int 
         int64_t prod = 1;
         for (int j = 0; j < p.Nm; ++j) prod *= b[j];
         for (int j = 0; j < p.Nm; ++j) {
-            if (b[j] >= p.n[j]) continue;
-            int64_t nb = std::min<int64_t>(2 * b[j], p.n[j]);
+            if (b[j] >= p.n[j] || b[j] >= SWEEP_BMAX) continue;
+            int64_t nb = std::min<int64_t>(std::min<int64_t>(2 * b[j], p.n[j]), SWEEP_BMAX);
             if (prod / b[j] * nb > target) continue;
             double r = (double)p.n[j] / b[j];
             if (r > bestr) { bestr = r; best = j; }
@@ -454,8 +467,10 @@ void count(Ctx &c) { c.launches++; c.phase_launches++; }
 
 cudaError_t run_groups(Ctx &c, const std::vector<Group> &gs, bool fp64, int which,
                        const void *first_in, int first_in_kind, void *work, int work_kind,
-                       void *last_out, int last_out_kind, int last_epi, const int *done) {
-    // which: 0 forward (U^*), 1 back (U)
+                       void *last_out, int last_out_kind, int last_epi, const int *done,
+                       const void *const *mats = nullptr, const void *aux = nullptr,
+                       cd scale = 1.0) {
+    // which: 0 forward (U^*), 1 back (U); `mats` replaces both (per mode)
     sylv_plan_s *p = c.p;
     for (size_t gi = 0; gi < gs.size(); ++gi) {
         const Group &g = gs[gi];
@@ -464,9 +479,13 @@ cudaError_t run_groups(Ctx &c, const std::vector<Group> &gs, bool fp64, int whic
         for (int m = 0; m < g.count; ++m) {
             int j = g.first + m;
             a.gn[m] = (int)p->n[j];
-            if (fp64) a.mats[m] = which == 0 ? p->Uh64[j] : p->U64[j];
+            if (mats) a.mats[m] = mats[j];
+            else if (fp64) a.mats[m] = which == 0 ? p->Uh64[j] : p->U64[j];
             else a.mats[m] = which == 0 ? p->Uh32[j] : p->U32[j];
         }
+        a.B = aux;
+        a.sig_re = scale.real();
+        a.sig_im = scale.imag();
         a.L = g.L; a.P = g.P; a.R = g.R; a.Lt = g.Lt; a.Rt = g.Rt; a.tilesL = g.tilesL;
         a.flags = c.flags;
         a.done = done;
@@ -504,8 +523,12 @@ cudaError_t run_groups(Ctx &c, const std::vector<Group> &gs, bool fp64, int whic
     return cudaSuccess;
 }
 
-cudaError_t run_residual(Ctx &c, const void *B, const void *X, void *R, const int *done) {
+// R = B - sigma X - sum_j M_j (x)_j X over the FP64 residual passes, M_j = A_j
+// (or the given per-mode matrices, with the given sigma)
+cudaError_t run_residual(Ctx &c, const void *B, const void *X, void *R, const int *done,
+                         const void *const *mats = nullptr, const cd *sig = nullptr) {
     sylv_plan_s *p = c.p;
+    const cd sg = sig ? *sig : p->sigma;
     for (size_t gi = 0; gi < p->rgroups.size(); ++gi) {
         const Group &g = p->rgroups[gi];
         MPArgs a{};
@@ -513,14 +536,14 @@ cudaError_t run_residual(Ctx &c, const void *B, const void *X, void *R, const in
         for (int m = 0; m < g.count; ++m) {
             int j = g.first + m;
             a.gn[m] = (int)p->n[j];
-            a.mats[m] = p->A64[j];
+            a.mats[m] = mats ? mats[j] : p->A64[j];
         }
         a.L = g.L; a.P = g.P; a.R = g.R; a.Lt = g.Lt; a.Rt = g.Rt; a.tilesL = g.tilesL;
         a.in = X;
         a.out = R;
         a.B = B;
-        a.sig_re = p->sigma.real();
-        a.sig_im = p->sigma.imag();
+        a.sig_re = sg.real();
+        a.sig_im = sg.imag();
         a.first = gi == 0;
         a.flags = c.flags;
         a.done = done;
@@ -551,7 +574,17 @@ cudaError_t run_sweep_cfg(Ctx &c, const SweepConfig &cfg, void *Y, bool fp64) {
     return cudaSuccess;
 }
 
-cudaError_t run_sweep(Ctx &c, void *Y, bool fp64) { return run_sweep_cfg(c, c.p->sweep, Y, fp64); }
+cudaError_t run_sweep(Ctx &c, void *Y, bool fp64) {
+    sylv_plan_s *p = c.p;
+    if (!p->diag_sweep) return run_sweep_cfg(c, p->sweep, Y, fp64);
+    DiagArgs a = p->diag;
+    a.Y = Y;
+    a.flags = c.flags;
+    cudaError_t e = launch_sweep_diag(fp64, a, p->num_sms, c.st);
+    if (e != cudaSuccess) return e;
+    count(c);
+    return cudaSuccess;
+}
 
 sylv_status check_ws(sylv_plan_s *p, void *ws, size_t bytes) {
     if (p->ws_bytes == 0) return SYLV_OK;
@@ -572,7 +605,7 @@ sylv_status fill_info(sylv_plan_s *p, DevFlags *flags, cudaStream_t st, sylv_inf
     info->status = s;
     info->refine_iters = p->fp64() ? 0 : h.iters;
     info->launches = launches;
-    info->reserved = 0;
+    info->path = p->diag_sweep ? 1 : 0;
     info->last_corr_rel = p->fp64() ? 0.0 : (double)h.lastcorr;
     info->est_rel_err = p->fp64() ? 0.0 : (double)h.est;
     info->min_abs_den = p->min_den;
@@ -804,6 +837,16 @@ sylv_status sylv_schur(int64_t n, const double *A, double *Q, double *T) {
     }
 }
 
+sylv_status sylv_expm(int64_t n, const double *M, double *E) {
+    if (!M || !E) return SYLV_ERR_INVALID_ARG;
+    if (n < 1 || n > MAX_N) return SYLV_ERR_SHAPE;
+    try {
+        return expm_host(n, M, E);
+    } catch (...) {
+        return SYLV_ERR_OOM;
+    }
+}
+
 sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t nrhs,
                              const double *const *A, const double *const *Q,
                              const double *const *T, int prec, double rtol, int max_refine,
@@ -896,6 +939,33 @@ sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t 
             if (!std::isfinite(z.real()) || !std::isfinite(z.imag())) return SYLV_ERR_INVALID_ARG;
         if (nj == 1) p->sigma += Tj[0];
     }
+    // Remark 1: when every A_j is normal its Schur factor T_j is diagonal up
+    // to rounding (||strict upper||_F of order n_j u ||T_j||_F); dropping that
+    // part perturbs A_j at the level of the Schur step's own backward error,
+    // and the sweep becomes an entrywise division
+    if (!(tuning && tuning->general_sweep) && p->Nm > 0) {
+        bool diag = true;
+        for (int j = 0; diag && j < p->Nm; ++j) {
+            const auto &Tj = p->Th[p->orig[j]];
+            const int64_t nj = p->n[j];
+            double off = 0.0, all = 0.0;
+            for (int64_t c = 0; c < nj; ++c)
+                for (int64_t r = 0; r <= c; ++r) {
+                    const double a2 = std::norm(Tj[(size_t)(r + c * nj)]);
+                    all += a2;
+                    if (r < c) off += a2;
+                }
+            diag = std::sqrt(off) <= 4.0 * (double)nj * std::ldexp(1.0, -53) * std::sqrt(all);
+        }
+        p->diag_sweep = diag;
+    }
+    int diag_h = 0;
+    int64_t diag_P1 = 1;
+    if (p->diag_sweep) {
+        diag_P1 = p->n[0];
+        diag_h = 1;
+        while (diag_h < p->Nm && diag_P1 * p->n[diag_h] <= DIAG_HEAD_MAX) diag_P1 *= p->n[diag_h++];
+    }
 
     // device
     {
@@ -923,6 +993,12 @@ sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t 
     if (s != SYLV_OK) return s;
     s = make_groups(*p, true, false, gmax, false, p->rgroups);
     if (s != SYLV_OK) return s;
+    if (p->fp64()) {
+        p->egroups = p->tgroups;
+    } else {
+        s = make_groups(*p, true, true, gmax, false, p->egroups);
+        if (s != SYLV_OK) return s;
+    }
     // device pool: per mode Uh64 U64 A64 T64 d64 Uh32 U32 T32, then the tables
     size_t off = 0;
     std::vector<size_t> offs;
@@ -932,8 +1008,11 @@ sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t 
         reserve(nn * 16); reserve(nn * 16); reserve(nn * 16); reserve(nn * 16);
         reserve((size_t)p->n[j] * 16);
         reserve(nn * 8); reserve(nn * 8); reserve(nn * 8);
+        reserve(nn * 16); reserve(nn * 16);              // -A_j, exp(t A_j)
     }
     reserve(3 * sizeof(unsigned long long));
+    const size_t diag_idx = offs.size();
+    if (p->diag_sweep) reserve((size_t)diag_P1 * 16);
     const size_t tc_first = offs.size();
     for (auto &g : p->tgroups)
         if (g.tc) {
@@ -987,7 +1066,11 @@ sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t 
         p->Uh32[j] = base + offs[oi + 5];
         p->U32[j] = base + offs[oi + 6];
         p->T32[j] = base + offs[oi + 7];
-        oi += 8;
+        double *na64 = (double *)(host.data() + offs[oi + 8]);
+        for (size_t k = 0; k < (size_t)(2 * nj * nj); ++k) na64[k] = -a64[k];
+        p->nA64[j] = base + offs[oi + 8];
+        p->E64[j] = base + offs[oi + 9];
+        oi += 10;
     }
     unsigned long long *dm = (unsigned long long *)(base + offs[oi]);
     unsigned long long init3[3] = {~0ull, 0ull, 0ull};
@@ -1029,6 +1112,31 @@ sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t 
             ti += 2;
         }
     }
+    // diagonal-sweep head table: sigma + sum of t_{j,i_j i_j} over the head modes
+    if (p->diag_sweep) {
+        double *tab = (double *)(host.data() + offs[diag_idx]);
+        for (int64_t q = 0; q < diag_P1; ++q) {
+            cd sum = p->sigma;
+            int64_t r = q;
+            for (int j = 0; j < diag_h; ++j) {
+                const int64_t i = r % p->n[j];
+                r /= p->n[j];
+                sum += p->Th[p->orig[j]][(size_t)(i + i * p->n[j])];
+            }
+            tab[2 * q] = sum.real();
+            tab[2 * q + 1] = sum.imag();
+        }
+        DiagArgs &d = p->diag;
+        d.total = p->ntot * p->nrhs;
+        d.P1 = diag_P1;
+        d.Qt = p->ntot / diag_P1;
+        d.dhead = (const double *)(base + offs[diag_idx]);
+        d.Nt = p->Nm - diag_h;
+        for (int m = 0; m < d.Nt; ++m) {
+            d.tn[m] = p->n[diag_h + m];
+            d.td[m] = p->d64[diag_h + m];
+        }
+    }
     if (cudaMemcpy(p->dpool, host.data(), pool_bytes, cudaMemcpyHostToDevice) != cudaSuccess)
         return SYLV_ERR_CUDA;
 
@@ -1046,6 +1154,7 @@ sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t 
     if (r3[2] != 0 || !(mn > 0.0) || !std::isfinite(mx)) return SYLV_ERR_SINGULAR;
     // power of two centring |scale * sum|^2 on 1 for the sweep's reciprocals
     p->den_scale = std::ldexp(1.0, -(int)std::lround(0.5 * (std::log2(mn) + std::log2(mx))));
+    p->diag.den_scale = p->den_scale;
 
     // sweep: default tiles (FP64 256 entries x 128 threads, FP32 1024 x 256,
     // measured on GB300) or the caller's block extents
@@ -1192,7 +1301,9 @@ sylv_status sylv_plan_autotune(sylv_plan_t p, void *Tdev, void *ws, size_t ws_by
         for (int rep = 0; rep < 3; ++rep) {          // first run warms up
             if (launch_solve_init(c.flags, st) != cudaSuccess) return false;
             if (cudaEventRecord(e0, st) != cudaSuccess) return false;
-            if (run_sweep_cfg(c, cfg, Tdev, p->fp64()) != cudaSuccess) return false;
+            if ((p->diag_sweep ? run_sweep(c, Tdev, p->fp64())
+                               : run_sweep_cfg(c, cfg, Tdev, p->fp64())) != cudaSuccess)
+                return false;
             if (cudaEventRecord(e1, st) != cudaSuccess) return false;
             if (cudaEventSynchronize(e1) != cudaSuccess) return false;
             float t = 0.f;
@@ -1204,7 +1315,8 @@ sylv_status sylv_plan_autotune(sylv_plan_t p, void *Tdev, void *ws, size_t ws_by
     };
     float cur_ms = 0.f;
     bool ok = time_cfg(p->sweep, cur_ms);
-    for (int target = 64; ok && target <= 2048; target *= 2) {
+    // the entrywise-division sweep (Remark 1) has no tiling to tune
+    for (int target = 64; ok && !p->diag_sweep && target <= 2048; target *= 2) {
         int b[MAXM];
         choose_blocks(*p, target, nullptr, b);
         if (tiles_for(*p, b) > p->cnt_capacity) continue;
@@ -1236,6 +1348,80 @@ sylv_status sylv_plan_autotune(sylv_plan_t p, void *Tdev, void *ws, size_t ws_by
         for (int j = 0, q = 0; j < p->N_in; ++j)
             block_out[j] = (q < p->Nm && p->orig[q] == j) ? p->sweep.a.b[q++] : 1;
     if (best_ms) *best_ms = cur_ms;
+    return SYLV_OK;
+}
+
+// ------------------------------------------------------------ Theorem 1 --
+
+sylv_status sylv_evolve_workspace_size(sylv_plan_t p, size_t *bytes) {
+    if (!p || !bytes) return SYLV_ERR_INVALID_ARG;
+    *bytes = align256(p->ws_bytes) + align256((size_t)(p->ntot * p->nrhs) * 16);
+    return SYLV_OK;
+}
+
+sylv_status sylv_evolve(sylv_plan_t p, double t, const void *B, const void *X0, void *X,
+                        void *ws, size_t ws_bytes, void *stream, sylv_info *info) {
+    if (!p || !B || !X0 || !X || !std::isfinite(t)) return SYLV_ERR_INVALID_ARG;
+    if ((((uintptr_t)B) | ((uintptr_t)X0) | ((uintptr_t)X)) & 15) return SYLV_ERR_INVALID_ARG;
+    size_t need = 0;
+    sylv_evolve_workspace_size(p, &need);
+    if (!ws || ws_bytes < need) return SYLV_ERR_WORKSPACE;
+    if (((uintptr_t)ws) & 255) return SYLV_ERR_INVALID_ARG;
+    DeviceGuard dg(p->device);
+    if (!dg.ok) return SYLV_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    // exp(t A_j) on the host (Pade scaling and squaring), uploaded in stream order
+    if (!p->evolve_ready || p->evolve_t != t) {
+        size_t tot = 0;
+        for (int j = 0; j < p->Nm; ++j) tot += (size_t)(2 * p->n[j] * p->n[j]);
+        p->Ehost.assign(tot, 0.0);
+        size_t o = 0;
+        for (int j = 0; j < p->Nm; ++j) {
+            const int64_t nj = p->n[j];
+            const auto &Aj = p->Ah[p->orig[j]];
+            std::vector<double> tA((size_t)(2 * nj * nj));
+            for (size_t k = 0; k < (size_t)(nj * nj); ++k) {
+                tA[2 * k] = t * Aj[k].real();
+                tA[2 * k + 1] = t * Aj[k].imag();
+            }
+            sylv_status s = expm_host(nj, tA.data(), p->Ehost.data() + o);
+            if (s != SYLV_OK) return s;
+            o += (size_t)(2 * nj * nj);
+        }
+        o = 0;
+        for (int j = 0; j < p->Nm; ++j) {
+            const size_t bytes = (size_t)(p->n[j] * p->n[j]) * 16;
+            if (cudaMemcpyAsync(const_cast<void *>(p->E64[j]), p->Ehost.data() + o, bytes,
+                                cudaMemcpyHostToDevice, st) != cudaSuccess)
+                return SYLV_ERR_CUDA;
+            o += bytes / 8;
+        }
+        p->evolve_eps = std::exp(t * p->sigma);
+        if (!std::isfinite(p->evolve_eps.real()) || !std::isfinite(p->evolve_eps.imag()))
+            return SYLV_ERR_INVALID_ARG;
+        p->evolve_t = t;
+        p->evolve_ready = true;
+    }
+    Ctx c{p, st, reinterpret_cast<DevFlags *>(ws),
+          reinterpret_cast<int *>((char *)ws + p->off_cnt)};
+    void *W = (char *)ws + align256(p->ws_bytes);
+    phase_begin(c, SYLV_PH_EVOLVE);
+    if (launch_solve_init(c.flags, st) != cudaSuccess) return SYLV_ERR_CUDA;
+    count(c);
+    // W = B + sigma X0 + sum_j A_j (x)_j X0  (residual passes with -A_j, -sigma)
+    const cd nsig = -p->sigma;
+    if (run_residual(c, B, X0, W, nullptr, p->nA64, &nsig) != cudaSuccess) return SYLV_ERR_CUDA;
+    // F = exp(t sigma) exp(t A_N) (x)_N ( ... exp(t A_1) (x)_1 W) - B, Eq. (C)
+    if (run_groups(c, p->egroups, true, 0, W, ELEM_C128, W, ELEM_C128, W, ELEM_C128, EPI_SUB,
+                   nullptr, p->E64, B, p->evolve_eps) != cudaSuccess)
+        return SYLV_ERR_CUDA;
+    phase_end(c);
+    // sum_j A_j (x)_j X(t) = F, Eq. (sylvesterNDC)
+    int launches = 0;
+    sylv_status s = solve_impl(p, W, X, ws, st, launches);
+    if (s != SYLV_OK) return s;
+    if (cudaGetLastError() != cudaSuccess) return SYLV_ERR_CUDA;
+    if (info) return fill_info(p, c.flags, st, info, c.launches + launches);
     return SYLV_OK;
 }
 

@@ -4,7 +4,8 @@
 //  k_modeprod  one transform pass: the mode-j products of Eq. (CUNU2U1B) /
 //              Eq. (XUNU2U1Y) for a group of adjacent modes, applied to a
 //              tile staged in shared memory; epilogues fuse the FP64 residual
-//              R = B - sum_j A_j (x)_j X and the refinement update X += D.
+//              R = B - sum_j A_j (x)_j X, the refinement update X += D, and
+//              the subtraction of B that ends Eq. (C) of Theorem 1.
 //  small       control kernels (flags, refinement decision, the plan-time
 //              scan of the diagonal sums t_{1,i1i1}+...+t_{N,iNiN}).
 #include <cuda_runtime.h>
@@ -160,6 +161,14 @@ __global__ void __launch_bounds__(256) k_modeprod(const __grid_constant__ MPArgs
             double2 o = to_c(acc, double());
             reinterpret_cast<double2 *>(a.out)[g] = o;
             nx = fmaxf(nx, cabsmax(o));
+        } else if (EPI == EPI_SUB) {
+            // Eq. (C): out = scale * (exp(tA) products) - B
+            const double2 b = reinterpret_cast<const double2 *>(a.B)[g];
+            const double2 v = to_c(acc, double());
+            double2 o;
+            o.x = (a.sig_re * v.x - a.sig_im * v.y) - b.x;
+            o.y = (a.sig_re * v.y + a.sig_im * v.x) - b.y;
+            reinterpret_cast<double2 *>(a.out)[g] = o;
         } else if (EPI == EPI_ACCUM) {
             double2 *Xp = reinterpret_cast<double2 *>(a.out);
             double2 x = Xp[g];
@@ -228,6 +237,8 @@ cudaError_t launch_modeprod(int fp64, int in_kind, int out_kind, int epi, const 
             k_modeprod<double, double2, double2, EPI_STORE><<<grid, block, smem, st>>>(a);
         else if (epi == EPI_RESID)
             k_modeprod<double, double2, double2, EPI_RESID><<<grid, block, smem, st>>>(a);
+        else if (epi == EPI_SUB)
+            k_modeprod<double, double2, double2, EPI_SUB><<<grid, block, smem, st>>>(a);
         else
             return cudaErrorInvalidValue;
     } else {
@@ -358,6 +369,7 @@ cudaError_t kernels_init(int) {
     cudaError_t e;
     if ((e = set_smem_attr<double, double2, double2, EPI_STORE>()) != cudaSuccess) return e;
     if ((e = set_smem_attr<double, double2, double2, EPI_RESID>()) != cudaSuccess) return e;
+    if ((e = set_smem_attr<double, double2, double2, EPI_SUB>()) != cudaSuccess) return e;
     if ((e = set_smem_attr<float, double2, float2, EPI_STORE>()) != cudaSuccess) return e;
     if ((e = set_smem_attr<float, float2, float2, EPI_STORE>()) != cudaSuccess) return e;
     if ((e = set_smem_attr<float, float2, double2, EPI_STORE_NORM>()) != cudaSuccess) return e;

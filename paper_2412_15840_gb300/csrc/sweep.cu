@@ -25,6 +25,7 @@
 //  3. store Y (L2), fence, release the counters of the predecessor tiles.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "cplx.cuh"
@@ -386,6 +387,82 @@ cudaError_t launch_sweep_init(const SweepArgs &a, cudaStream_t st) {
     if (blocks < 1) blocks = 1;
     if (blocks > 4096) blocks = 4096;
     k_sweep_init<<<(unsigned)blocks, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------- diagonal sweep --
+// Remark 1: with every T_j diagonal the sweep has no dependencies and is the
+// entrywise (Hadamard) division y = c / (sigma + sum_j t_{j,i_j i_j}) of
+// Eq. (yi1i2iNdiag).  One pass over the tensor, HBM-bound: each block takes
+// DIAG_CHUNK consecutive entries (8 per thread, loads issued together), the
+// tail sums of the columns it touches are decoded once into shared memory,
+// and the head sums come from the plan's table.  The sum and its reciprocal
+// are FP64; the FP32 path multiplies in FP64 and rounds once.
+constexpr int DIAG_THREADS = 256;
+constexpr int DIAG_PER = 8;
+constexpr int DIAG_CHUNK = DIAG_THREADS * DIAG_PER;
+constexpr int DIAG_MAXCOL = DIAG_CHUNK / 2 + 2;   // head product >= 2
+
+template <typename real>
+__global__ void __launch_bounds__(DIAG_THREADS) k_sweep_diag(const __grid_constant__ DiagArgs a) {
+    using C2 = typename C2T<real>::type;
+    if (*(volatile const int *)&a.flags->done) return;
+    __shared__ double2 dt[DIAG_MAXCOL];
+    C2 *Y = reinterpret_cast<C2 *>(a.Y);
+    const double2 *dh = reinterpret_cast<const double2 *>(a.dhead);
+    const int P1 = (int)a.P1;
+    for (int64_t start = (int64_t)blockIdx.x * DIAG_CHUNK; start < a.total;
+         start += (int64_t)gridDim.x * DIAG_CHUNK) {
+        const int64_t end = min(start + (int64_t)DIAG_CHUNK, a.total);
+        const int64_t q0 = start / P1;
+        const int ncol = (int)((end - 1) / P1 - q0) + 1;
+        for (int c = threadIdx.x; c < ncol; c += DIAG_THREADS) {
+            int64_t q = (q0 + c) % a.Qt;
+            double x = 0.0, y = 0.0;
+            for (int m = 0; m < a.Nt; ++m) {
+                const int64_t i = q % a.tn[m];
+                q /= a.tn[m];
+                x += a.td[m][2 * i];
+                y += a.td[m][2 * i + 1];
+            }
+            dt[c] = make_double2(x, y);
+        }
+        __syncthreads();
+        const int p0 = (int)(start - q0 * P1);
+        C2 v[DIAG_PER];
+#pragma unroll
+        for (int k = 0; k < DIAG_PER; ++k) {
+            const int64_t e = start + threadIdx.x + k * DIAG_THREADS;
+            if (e < end) v[k] = __ldcs(Y + e);
+        }
+#pragma unroll
+        for (int k = 0; k < DIAG_PER; ++k) {
+            const int64_t e = start + threadIdx.x + k * DIAG_THREADS;
+            if (e < end) {
+                const int off = p0 + threadIdx.x + k * DIAG_THREADS;
+                const int c = off / P1;
+                const double2 h = __ldg(dh + (off - c * P1));
+                const double2 inv = crecip_scaled(h.x + dt[c].x, h.y + dt[c].y, a.den_scale);
+                const double2 cv = to_c(v[k], 0.0);
+                double2 r;
+                r.x = fma(cv.x, inv.x, -cv.y * inv.y);
+                r.y = fma(cv.x, inv.y, cv.y * inv.x);
+                __stcs(Y + e, to_c(r, real(0)));
+            }
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_sweep_diag(int fp64, const DiagArgs &a, int num_sms, cudaStream_t st) {
+    if (a.total <= 0) return cudaSuccess;
+    if (a.P1 < 2 || a.P1 > DIAG_HEAD_MAX) return cudaErrorInvalidValue;
+    const int64_t chunks = (a.total + DIAG_CHUNK - 1) / DIAG_CHUNK;
+    const int grid = (int)std::min<int64_t>(chunks, (int64_t)num_sms * 8);
+    if (fp64)
+        k_sweep_diag<double><<<grid, DIAG_THREADS, 0, st>>>(a);
+    else
+        k_sweep_diag<float><<<grid, DIAG_THREADS, 0, st>>>(a);
     return cudaGetLastError();
 }
 

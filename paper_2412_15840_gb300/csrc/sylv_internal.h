@@ -17,8 +17,11 @@ constexpr int MAXM = 40;   // modes with n_j > 1 (after singleton removal)
 constexpr int MAXG = 16;   // modes fused into one transform pass
 constexpr int MAX_N = 1024;
 constexpr int SWEEP_KCH = 64;  // columns of T_j staged per chunk by the sweep
+constexpr int SWEEP_BMAX = 64; // automatic tile extents stay <= 64 per mode, so the
+                               // tile's diagonal T blocks fit in shared memory
 
 sylv_status schur_host(int64_t n, const double *A, double *Q, double *T);
+sylv_status expm_host(int64_t n, const double *M, double *E);
 
 // Device-side control block at the start of every workspace.
 struct DevFlags {
@@ -37,7 +40,7 @@ static_assert(sizeof(DevFlags) == 64, "DevFlags layout");
 
 enum { ERRBIT_TIMEOUT = 1, ERRBIT_NOTCONV = 2, ERRBIT_NAN = 4 };
 
-enum Epi { EPI_STORE = 0, EPI_RESID = 1, EPI_ACCUM = 2, EPI_STORE_NORM = 3 };
+enum Epi { EPI_STORE = 0, EPI_RESID = 1, EPI_ACCUM = 2, EPI_STORE_NORM = 3, EPI_SUB = 4 };
 enum ElemKind { ELEM_C64 = 0, ELEM_C128 = 1 };
 
 // One transform pass over the view (L, P, R) of a tensor, where P is the
@@ -51,7 +54,8 @@ struct MPArgs {
     int Lt, Rt;
     int64_t L, P, R;
     int64_t tilesL;
-    // residual: R = (first ? B - sigma*X : R) - sum_m A_m (x)_m X
+    // residual: R = (first ? B - sigma*X : R) - sum_m A_m (x)_m X;
+    // EPI_SUB: out = sigma * (product) - B
     const void *B;
     double sig_re, sig_im;
     int first;
@@ -93,6 +97,25 @@ struct SweepArgs {
     int fault_tile;           // test hook: this tile never releases its predecessors (-1: none)
 };
 
+// Sweep of a plan whose T_j are all diagonal (every A_j normal, Remark 1):
+// y = c / (sigma + sum_j t_{j,i_j i_j}), Eq. (yi1i2iNdiag).  The leading
+// modes whose size product P1 is at most DIAG_HEAD_MAX share one table of
+// partial diagonal sums; the remaining ("tail") modes are decoded per column
+// of P1 consecutive entries.
+constexpr int64_t DIAG_HEAD_MAX = 4096;
+struct DiagArgs {
+    void *Y;
+    int64_t total;            // ntot * nrhs entries
+    int64_t P1;               // product of the head modes' sizes
+    int64_t Qt;               // ntot / P1 (tail index range without the right-hand sides)
+    const double *dhead;      // P1 complex FP64: sigma + sum over the head modes
+    int Nt;                   // tail modes
+    int64_t tn[MAXM];
+    const double *td[MAXM];   // diag(T_j) of the tail modes, interleaved FP64
+    double den_scale;
+    DevFlags *flags;
+};
+
 // Tensor-core (tcgen05, 3xTF32) transform pass over one mode, complex64 in.
 struct TCArgs {
     const float *in;              // complex64 tensor, interleaved floats
@@ -115,6 +138,7 @@ cudaError_t launch_modeprod(int fp64, int in_kind, int out_kind, int epi, const 
 cudaError_t launch_sweep(int fp64, const SweepArgs &a, int grid, int threads, size_t smem,
                          cudaStream_t st);
 cudaError_t launch_sweep_init(const SweepArgs &a, cudaStream_t st);
+cudaError_t launch_sweep_diag(int fp64, const DiagArgs &a, int num_sms, cudaStream_t st);
 cudaError_t launch_solve_init(DevFlags *f, cudaStream_t st);
 cudaError_t launch_refine_decide(DevFlags *f, float rtol, int step, int max_refine,
                                  cudaStream_t st);

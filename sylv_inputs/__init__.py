@@ -7,7 +7,7 @@ This module is shared by the CPU oracle, the CUDA parity tests and the
 benchmark.  It holds no arithmetic of the solution method: it only draws
 coefficient matrices and right-hand sides from `numpy.random.default_rng`.
 
-Layout conventions (Section 3, Eq. (index)): tensors are column-major with
+Layout conventions (Section 2.2, Eq. (index)): tensors are column-major with
 i_1 fastest; complex values are stored interleaved (re, im) as complex128.
 A right-hand-side index, when present, is one extra trailing axis.
 
@@ -177,3 +177,10 @@ def manufactured(shape: Sequence[int], nrhs: int = 1, seed: int = 0,
     rng = np.random.default_rng(seed + 7919)
     X = complex_gaussian(rng, tuple(shape) + (nrhs,))
     return p.A, X
+
+
+def initial_state(shape: Sequence[int], nrhs: int = 1, seed: int = 1) -> np.ndarray:
+    """Initial value X(0) for the ODE X_t = sum_j A_j (x)_j X + B (Theorem 1):
+    a unit-variance complex Gaussian tensor from its own seeded stream."""
+    full = tuple(shape) + ((nrhs,) if nrhs > 1 else ())
+    return complex_gaussian(np.random.default_rng(seed), full)

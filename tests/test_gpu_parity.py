@@ -65,6 +65,8 @@ SHAPES = [
     ((2, 1, 3), 1), ((1, 6, 1, 5), 2), ((8, 8, 8), 1), ((17, 11, 9), 2),
     ((33, 5, 7), 1), ((2, 2, 2, 2, 2, 2, 2, 2, 2, 2), 1), ((3, 1, 4, 1, 5, 2), 3),
     ((70, 3), 1), ((9, 10, 11, 3), 1), ((100, 2, 2), 1),
+    # modes longer than the largest automatic tile extent (64)
+    ((600, 9), 1), ((130, 3, 2), 2),
 ]
 
 

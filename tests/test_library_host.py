@@ -75,3 +75,39 @@ def test_host_schur_special_matrices():
 def test_host_schur_rejects_bad_input():
     with pytest.raises(pkg.SylvError):
         pkg.schur(np.full((3, 3), np.nan + 0j))
+
+
+@pytest.mark.parametrize("n,scale,seed", [(1, 0.5, 0), (2, 0.01, 1), (5, 1.0, 2), (12, 4.0, 3),
+                                          (33, 0.3, 4), (40, 9.0, 5)])
+def test_host_expm_matches_scipy(n, scale, seed):
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    rng = np.random.default_rng(seed)
+    M = scale * (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / np.sqrt(n)
+    E = pkg.expm(M)
+    ref = scipy_linalg.expm(M)
+    assert np.linalg.norm(E - ref) <= 1e-13 * np.linalg.norm(ref)
+    mpmath = pytest.importorskip("mpmath")
+    with mpmath.workdps(40):
+        exact = np.array(mpmath.expm(mpmath.matrix(M.tolist())).tolist(), dtype=np.complex128)
+    assert np.linalg.norm(E - exact) <= 1e-14 * np.linalg.norm(exact)
+    if scale <= 1.0:      # exp(M) exp(-M) = I, where exp(-M) is not huge
+        assert np.linalg.norm(E @ pkg.expm(-M) - np.eye(n)) < 1e-13
+
+
+def test_host_expm_closed_forms():
+    lam = np.array([0.3 + 1j, -2.0, 1.5 - 0.5j, 4.0j])
+    assert np.allclose(pkg.expm(np.diag(lam)), np.diag(np.exp(lam)), rtol=1e-14, atol=1e-15)
+    # nilpotent: exp(J) = I + J + J^2/2 for a strictly upper 3x3 J
+    J = np.array([[0, 2.0, -1.0], [0, 0, 3.0], [0, 0, 0]], dtype=np.complex128)
+    assert np.allclose(pkg.expm(J), np.eye(3) + J + J @ J / 2, rtol=0, atol=1e-14)
+    # 2x2 rotation generator: exp([[0, -w], [w, 0]]) = rotation by w
+    w = 0.7
+    R = pkg.expm(np.array([[0, -w], [w, 0]], dtype=np.complex128))
+    assert np.allclose(R, [[np.cos(w), -np.sin(w)], [np.sin(w), np.cos(w)]], atol=1e-15)
+    assert np.array_equal(pkg.expm(np.zeros((4, 4))), np.eye(4))
+
+
+def test_host_expm_rejects_bad_input():
+    with pytest.raises(binding.SylvError) as e:
+        pkg.expm(np.array([[np.nan]]))
+    assert e.value.status == 1
