@@ -234,6 +234,8 @@ def evolve_rhs(A: Sequence[np.ndarray], B: np.ndarray, X0: np.ndarray, t: float)
 
     The matrix exponentials are scipy's (a library primitive); the mode
     products are applied in the order 1..N written in Eq. (C)."""
+    if np.shape(X0) != np.shape(B):
+        raise ValueError("X0 and B must have the same shape")
     W = apply_operator(A, X0) + B
     for j, a in enumerate(A):
         W = mode_product(scipy.linalg.expm(t * np.asarray(a, dtype=np.complex128)), W, j)

@@ -30,26 +30,49 @@ struct Group {
     // tensor-core pass (one mode): operand geometry and the B images of
     // U^* (forward) and U (back) in the device pool
     int tc = 0;
-    int Kp = 0, Np = 0, sboA = 0, sboB = 0, bimg_bytes = 0, tmem_cols = 0;
+    int mode1 = 0;                // first mode (L = 1): tiles of 64 columns
+    int Kp = 0, Np = 0, lboA = 0, sboA = 0, sboB = 0, abytes = 0, bimg_bytes = 0;
+    int tmem_cols = 0, nbuf = 1;
     const unsigned char *img[2] = {nullptr, nullptr};
 };
 
 // A mode runs on the tensor cores when its tile holds 64 complex positions
 // along the preceding modes and the operands fit in shared memory.
 bool tc_mode_ok(int64_t L, int64_t n) { return L >= 64 && n >= 32 && n <= 80; }
+// The first mode (contiguous fibres) runs on the tensor cores with tiles of 64
+// columns when it is not the last pass of a transform and n is a multiple of 8.
+bool tc_mode1_ok(int64_t n, int64_t cols, int Nm) {
+    return Nm >= 2 && n % 8 == 0 && n >= 32 && n <= 80 && cols >= 64;
+}
 
-void tc_geometry(Group &g, int n) {
+void tc_geometry(Group &g, int n, bool mode1) {
     g.tc = 1;
+    g.mode1 = mode1 ? 1 : 0;
     g.Kp = (n + 7) / 8 * 8;
     g.Np = (2 * n + 15) / 16 * 16;
     g.sboB = g.Kp * 32;
-    g.sboA = g.Kp * 32 + 16;                   // padding: conflict-free staging stores
+    if (mode1) {
+        // 8-row groups adjacent, K-adjacent core matrices one padded column of
+        // 16 groups apart: the staging stores (lanes along k) are conflict-free
+        g.sboA = 128;
+        g.lboA = 16 * 128 + 16;
+        g.abytes = (g.Kp / 4) * g.lboA;
+    } else {
+        g.lboA = 128;
+        g.sboA = g.Kp * 32 + 16;               // padding: conflict-free staging stores
+        g.abytes = 16 * g.sboA;
+    }
     g.bimg_bytes = (g.Np / 8) * g.sboB;
     int need = std::max(g.Np, n + 16 * ((n + 15) / 16));
     int cols = 32;
     while (cols < need) cols *= 2;
     g.tmem_cols = cols;
-    g.smem = (size_t)2 * g.bimg_bytes + (size_t)2 * 16 * g.sboA;
+    // two A buffers and accumulators (MMAs of the next tile overlap the
+    // current tile's epilogue) when they fit next to the B images
+    const size_t one = (size_t)2 * g.abytes;
+    const size_t slack = mode1 ? 4096 : 0;     // keeps the padded A images inside the allocation
+    g.nbuf = (size_t)2 * g.bimg_bytes + 2 * one + slack <= (size_t)TC_SMEM_MAX ? 2 : 1;
+    g.smem = (size_t)2 * g.bimg_bytes + (size_t)g.nbuf * one + slack;
 }
 
 struct TimedPhase {
@@ -209,12 +232,13 @@ sylv_status make_groups(const sylv_plan_s &p, bool fp64, bool composition, int g
         Group g;
         g.first = j;
         g.L = p.S[j];
-        if (use_tc && tc_mode_ok(g.L, p.n[j])) {
+        const bool m1 = use_tc && j == 0 && tc_mode1_ok(p.n[0], tot / p.n[0], p.Nm);
+        if (m1 || (use_tc && tc_mode_ok(g.L, p.n[j]))) {
             g.count = 1;
             g.P = p.n[j];
             g.R = tot / (g.L * g.P);
-            g.tilesL = (g.L + 63) / 64;
-            tc_geometry(g, (int)p.n[j]);
+            g.tilesL = m1 ? 1 : (g.L + 63) / 64;
+            tc_geometry(g, (int)p.n[j], m1);
             out.push_back(g);
             j += 1;
             continue;
@@ -497,19 +521,25 @@ cudaError_t run_groups(Ctx &c, const std::vector<Group> &gs, bool fp64, int whic
         int epi = last ? last_epi : EPI_STORE;
         if (g.count == 0 && a.in == a.out && epi == EPI_STORE) continue;   // identity
         if (g.tc) {
-            if (in_kind != ELEM_C64) return cudaErrorInvalidValue;
+            if (in_kind != ELEM_C64 && !(g.mode1 && in_kind == ELEM_C128))
+                return cudaErrorInvalidValue;
+            if (mats) return cudaErrorInvalidValue;   // B images hold U^* and U only
             TCArgs t{};
-            t.in = reinterpret_cast<const float *>(a.in);
+            t.in = a.in;
             t.out = a.out;
             t.bimg = g.img[which];
             t.n = (int)g.P;
-            t.Kp = g.Kp; t.Np = g.Np; t.sboA = g.sboA; t.sboB = g.sboB;
+            t.mode1 = g.mode1;
+            t.in_c128 = in_kind == ELEM_C128 ? 1 : 0;
+            t.Kp = g.Kp; t.Np = g.Np; t.lboA = g.lboA; t.sboA = g.sboA; t.sboB = g.sboB;
+            t.abytes = g.abytes;
             t.bimg_bytes = g.bimg_bytes;
             t.tmem_cols = g.tmem_cols;
+            t.nbuf = g.nbuf;
             t.L = g.L; t.R = g.R; t.tilesL = g.tilesL;
             t.flags = c.flags;
             t.done = done;
-            const int64_t tiles = g.tilesL * g.R;
+            const int64_t tiles = g.mode1 ? (g.R + 63) / 64 : g.tilesL * g.R;
             const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, p->num_sms));
             cudaError_t e = launch_modeprod_tc(epi, t, grid, g.smem, c.st);
             if (e != cudaSuccess) return e;

@@ -82,13 +82,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
-// bounded wait on an mbarrier phase; false after ~2^24 polls
+// bounded wait on an mbarrier phase: false after ~2 s of SM clock (a
+// try_wait may itself suspend the thread for a while, so the bound is in time,
+// not in polls)
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    for (int it = 0; it < (1 << 24); ++it) {
+    const long long t0 = clock64();
+    for (int it = 0;; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
+        if (clock64() - t0 > 4000000000LL) return false;
         if (it > 64) __nanosleep(32);
     }
-    return false;
 }
 
 __device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols) {
@@ -172,40 +175,49 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
            ((uint32_t)(M >> 4) << 24);
 }
 
-// byte offset of element (row, k) in a K-major, no-swizzle operand
-__device__ __forceinline__ uint32_t kmaj_off(int row, int k, uint32_t sbo) {
-    return (uint32_t)(row >> 3) * sbo + (uint32_t)(k >> 2) * 128u + (uint32_t)(row & 7) * 16u +
-           (uint32_t)(k & 3) * 4u;
-}
 
 }  // namespace
 
-constexpr int TC_NU = 20;     // staging units per warp: Kp / 4 <= 20 for n <= 80
+constexpr int TC_THREADS = 256;  // 8 warps: two per TMEM lane quadrant
+constexpr int TC_NU = 10;        // staging units per thread: 32 n / 256 <= 10 for n <= 80
 
-template <int EPI>
-__global__ void __launch_bounds__(128, 1) k_modeprod_tc(const __grid_constant__ TCArgs a) {
+// byte offset of element (row, k) in a K-major, no-swizzle operand with
+// K-adjacent core matrices `lbo` bytes apart and 8-row groups `sbo` apart
+__device__ __forceinline__ uint32_t kmaj_off2(int row, int k, uint32_t lbo, uint32_t sbo) {
+    return (uint32_t)(row >> 3) * sbo + (uint32_t)(k >> 2) * lbo + (uint32_t)(row & 7) * 16u +
+           (uint32_t)(k & 3) * 4u;
+}
+
+// M1 = 0: modes with L >= 64 (tile rows: 64 consecutive l, re/im interleaved);
+// M1 = 1: the first mode (tile rows: 64 consecutive columns r).  IN128: the
+// input is complex128 (first forward pass of the first mode).
+template <int EPI, int M1, int IN128>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_modeprod_tc(const __grid_constant__ TCArgs a) {
     extern __shared__ __align__(128) unsigned char sm[];
     __shared__ __align__(8) uint64_t mbar_b;
-    __shared__ __align__(8) uint64_t mbar_mma;
+    __shared__ __align__(8) uint64_t mbar_mma[2];
     __shared__ uint32_t tmem_base_s;
     __shared__ int s_fail;
     if (a.done && *(volatile const int *)a.done) return;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int n = a.n, Kp = a.Kp;
+    const int nbuf = a.nbuf;
+    const uint32_t abytes = (uint32_t)a.abytes;             // one A image (hi or lo)
+    const uint32_t lboA = (uint32_t)a.lboA, sboA = (uint32_t)a.sboA;
     unsigned char *Bhi = sm;
     unsigned char *Blo = sm + a.bimg_bytes;
-    unsigned char *Ahi = sm + 2 * a.bimg_bytes;
-    unsigned char *Alo = Ahi + 16 * a.sboA;
+    unsigned char *Abase = sm + 2 * a.bimg_bytes;             // buffer b: hi, lo at 2 b abytes
 
     if (tid == 0) {
         s_fail = 0;
         mbar_init(&mbar_b, 1);
-        mbar_init(&mbar_mma, 1);
+        mbar_init(&mbar_mma[0], 1);
+        mbar_init(&mbar_mma[1], 1);
         fence_mbar_init();
     }
     if (warp == 0) {
-        tmem_alloc(&tmem_base_s, (uint32_t)a.tmem_cols);
+        tmem_alloc(&tmem_base_s, (uint32_t)(a.tmem_cols * nbuf));
         tmem_relinquish();
     }
     tc_fence_before();
@@ -222,26 +234,53 @@ __global__ void __launch_bounds__(128, 1) k_modeprod_tc(const __grid_constant__ 
     __syncthreads();
 
     const uint32_t idesc = idesc_tf32(128, a.Np);
-    const uint32_t ahi = smem_u32(Ahi), alo = smem_u32(Alo);
     const uint32_t bhi = smem_u32(Bhi), blo = smem_u32(Blo);
     const int64_t L = a.L;
     const bool evenL = (L & 1) == 0;
-    const int64_t ntile = a.tilesL * a.R;
-    uint32_t phase = 0;
+    const int64_t ntile = M1 ? (a.R + 63) / 64 : a.tilesL * a.R;
+    const int half_n = n >> 1;
+    uint32_t phase[2] = {0u, 0u};
     float nd = 0.f, nx = 0.f;
 
-    // A of the next tile is fetched into registers while the current tile's
-    // MMAs and epilogue run (TC_NU units of 8 float4 x 4 k per warp, Kp <= 80)
+    // The tile's values are fetched into registers one tile ahead.
+    //  M1 = 0: unit b of a thread: float4 index m4 (4 rows) along the 128 rows
+    //          at one k (lanes along m4: coalesced along l);
+    //  M1 = 1: unit b: flat float4 f = tid + 256 b of the contiguous tile,
+    //          column p = f / (n/2), entries k = 2 (f % (n/2)) and k + 1.
     float x[TC_NU][4];
     auto fetch = [&](int64_t t) {
+        if (M1) {
+            const int64_t p0 = t * 64;
+            const int lvv = (int)((a.R - p0) < 64 ? (a.R - p0) : 64);
+#pragma unroll
+            for (int b = 0; b < TC_NU; ++b) {
+                const int f = tid + TC_THREADS * b;
+                const int p = f / half_n, k = 2 * (f - p * half_n);
+                x[b][0] = x[b][1] = x[b][2] = x[b][3] = 0.f;
+                if (p < lvv) {
+                    const int64_t e = (p0 + p) * n + k;       // complex index
+                    if (IN128) {
+                        const double2 *src = reinterpret_cast<const double2 *>(a.in) + e;
+                        const double2 v0 = __ldg(src), v1 = __ldg(src + 1);
+                        x[b][0] = (float)v0.x; x[b][1] = (float)v0.y;
+                        x[b][2] = (float)v1.x; x[b][3] = (float)v1.y;
+                    } else {
+                        const float4 v = __ldg(reinterpret_cast<const float4 *>(
+                            reinterpret_cast<const float2 *>(a.in) + e));
+                        x[b][0] = v.x; x[b][1] = v.y; x[b][2] = v.z; x[b][3] = v.w;
+                    }
+                }
+            }
+            return;
+        }
         const int64_t rr = t / a.tilesL;
         const int64_t ll0 = (t % a.tilesL) * 64;
         const int lvv = (int)((L - ll0) < 64 ? (L - ll0) : 64);
-        const float *src = a.in + 2 * (ll0 + rr * L * n);
+        const float *src = reinterpret_cast<const float *>(a.in) + 2 * (ll0 + rr * L * n);
 #pragma unroll
         for (int b = 0; b < TC_NU; ++b) {
-            const int u = warp + 4 * b;
-            const int m4 = (u & 3) * 8 + (lane & 7);      // float4 index along the 128 rows
+            const int u = warp + 8 * b;
+            const int m4 = (u & 3) * 8 + (lane & 7);
             const int k = (u >> 2) * 4 + (lane >> 3);
             x[b][0] = x[b][1] = x[b][2] = x[b][3] = 0.f;
             if (u < Kp && k < n) {
@@ -264,55 +303,112 @@ __global__ void __launch_bounds__(128, 1) k_modeprod_tc(const __grid_constant__ 
             }
         }
     };
-    if ((int64_t)blockIdx.x < ntile) fetch(blockIdx.x);
-
-    for (int64_t tile = blockIdx.x; tile < ntile && !s_fail; tile += gridDim.x) {
-        const int64_t r = tile / a.tilesL;
-        const int64_t l0 = (tile % a.tilesL) * 64;
-        const int lv = (int)((L - l0) < 64 ? (L - l0) : 64);
-
-        // stage A: split the fetched values into TF32 hi and lo
+    // split the fetched values into TF32 hi and lo in A buffer `buf`
+    auto stage = [&](int buf) {
+        unsigned char *Ahi = Abase + 2u * buf * abytes;
+        unsigned char *Alo = Ahi + abytes;
 #pragma unroll
         for (int b = 0; b < TC_NU; ++b) {
-            const int u = warp + 4 * b;
+            if (M1) {
+                // (re_k, im_k, re_k+1, im_k+1) of column p -> rows 2p (re), 2p+1 (im)
+                const int f = tid + TC_THREADS * b;
+                const int p = f / half_n, k = 2 * (f - p * half_n);
+                if (p >= 64) continue;
+                float h[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) h[j] = tf32_rna(x[b][j]);
+                const uint32_t o0 = kmaj_off2(2 * p, k, lboA, sboA);
+                *reinterpret_cast<float2 *>(Ahi + o0) = make_float2(h[0], h[2]);
+                *reinterpret_cast<float2 *>(Ahi + o0 + 16) = make_float2(h[1], h[3]);
+                *reinterpret_cast<float2 *>(Alo + o0) =
+                    make_float2(x[b][0] - h[0], x[b][2] - h[2]);
+                *reinterpret_cast<float2 *>(Alo + o0 + 16) =
+                    make_float2(x[b][1] - h[1], x[b][3] - h[3]);
+                continue;
+            }
+            const int u = warp + 8 * b;
             if (u >= Kp) continue;
             const int m4 = (u & 3) * 8 + (lane & 7);
             const int k = (u >> 2) * 4 + (lane >> 3);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const float h = tf32_rna(x[b][j]);
-                const uint32_t off = kmaj_off(4 * m4 + j, k, (uint32_t)a.sboA);
+                const uint32_t off = kmaj_off2(4 * m4 + j, k, lboA, sboA);
                 *reinterpret_cast<float *>(Ahi + off) = h;
                 *reinterpret_cast<float *>(Alo + off) = x[b][j] - h;
             }
         }
         fence_proxy_async_smem();
-        __syncthreads();
-
-        if (tid == 0) {
-            tc_fence_after();
-            const int steps = Kp / 8;
-            for (int s = 0; s < steps; ++s)     // small terms first
-                mma_tf32(tmem, smem_desc(alo + 256u * s, 128u, (uint32_t)a.sboA),
-                         smem_desc(bhi + 256u * s, 128u, (uint32_t)a.sboB), idesc, s > 0);
-            for (int s = 0; s < steps; ++s)
-                mma_tf32(tmem, smem_desc(ahi + 256u * s, 128u, (uint32_t)a.sboA),
-                         smem_desc(blo + 256u * s, 128u, (uint32_t)a.sboB), idesc, 1u);
-            for (int s = 0; s < steps; ++s)
-                mma_tf32(tmem, smem_desc(ahi + 256u * s, 128u, (uint32_t)a.sboA),
-                         smem_desc(bhi + 256u * s, 128u, (uint32_t)a.sboB), idesc, 1u);
-            mma_commit(&mbar_mma);
-        }
-        if (tile + gridDim.x < ntile) fetch(tile + gridDim.x);
-        if (!mbar_wait(&mbar_mma, phase)) s_fail = 1;
-        phase ^= 1u;
+    };
+    // one thread: D[acc] = A_lo B_hi + A_hi B_lo + A_hi B_hi, small terms first;
+    // a K step (8 TF32) spans two K-adjacent core matrices
+    auto issue = [&](int buf) {
+        const uint32_t ahi = smem_u32(Abase + 2u * buf * abytes), alo = ahi + abytes;
+        const uint32_t d = tmem + (uint32_t)(buf * a.tmem_cols);
+        const uint32_t ka = 2u * lboA;
         tc_fence_after();
-
-        // epilogue: TMEM lane m = 32 warp + lane holds row (l, c) = (m / 2, m % 2)
-        const int m = 32 * warp + lane;
-        const int ll = m >> 1, c = m & 1;
-        const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
-        for (int i0 = 0; i0 < n; i0 += 16) {
+        const int steps = Kp / 8;
+        for (int s = 0; s < steps; ++s)
+            mma_tf32(d, smem_desc(alo + ka * s, lboA, sboA),
+                     smem_desc(bhi + 256u * s, 128u, (uint32_t)a.sboB), idesc, s > 0);
+        for (int s = 0; s < steps; ++s)
+            mma_tf32(d, smem_desc(ahi + ka * s, lboA, sboA),
+                     smem_desc(blo + 256u * s, 128u, (uint32_t)a.sboB), idesc, 1u);
+        for (int s = 0; s < steps; ++s)
+            mma_tf32(d, smem_desc(ahi + ka * s, lboA, sboA),
+                     smem_desc(bhi + 256u * s, 128u, (uint32_t)a.sboB), idesc, 1u);
+        mma_commit(&mbar_mma[buf]);
+    };
+    // TMEM lane m = 32 (warp & 3) + lane holds row (p, c) = (m / 2, m % 2) of the
+    // tile; the two warps of a lane quadrant take alternate 16-column chunks
+    const int q = warp & 3, half = warp >> 2;
+    const int m = 32 * q + lane;
+    const int ll = m >> 1, cc = m & 1;
+    auto epilogue = [&](int64_t t, int buf) {
+        const uint32_t trow = tmem + (uint32_t)(buf * a.tmem_cols) + ((uint32_t)(32 * q) << 16);
+        if (M1) {
+            // complex64 out[p, i]: after one exchange with the partner lane, lane
+            // c holds out[p, i0 + 8c .. i0 + 8c + 7] (64 contiguous bytes)
+            const int64_t p0 = t * 64;
+            const bool live = p0 + ll < a.R;
+            float2 *orow = reinterpret_cast<float2 *>(a.out) + (p0 + ll) * n;
+            for (int i0 = 16 * half; i0 < n; i0 += 32) {
+                uint32_t va[16], vb[16];
+                tmem_ld16(trow + (uint32_t)i0, va);
+                tmem_ld16(trow + (uint32_t)(n + i0), vb);
+                tmem_wait_ld();
+                float o[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const float av = __uint_as_float(va[j]);
+                    const float pb = __shfl_xor_sync(0xffffffffu, __uint_as_float(vb[j]), 1);
+                    o[j] = cc == 0 ? av - pb : av + pb;
+                }
+                float4 w[4];
+#pragma unroll
+                for (int t2 = 0; t2 < 8; ++t2) {
+                    const float send = cc == 0 ? o[8 + t2] : o[t2];
+                    const float recv = __shfl_xor_sync(0xffffffffu, send, 1);
+                    const float re = cc == 0 ? o[t2] : recv;
+                    const float im = cc == 0 ? recv : o[8 + t2];
+                    if (t2 & 1) { w[t2 >> 1].z = re; w[t2 >> 1].w = im; }
+                    else { w[t2 >> 1].x = re; w[t2 >> 1].y = im; }
+                }
+                const int ib = i0 + 8 * cc;
+                if (live && ib < n) {
+                    float4 *dst = reinterpret_cast<float4 *>(orow + ib);
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) dst[v] = w[v];
+                }
+            }
+            return;
+        }
+        const int64_t r = t / a.tilesL;
+        const int64_t l0 = (t % a.tilesL) * 64;
+        const int lv = (int)((L - l0) < 64 ? (L - l0) : 64);
+        const bool live = ll < lv;
+        const int64_t base = 2 * (l0 + ll + r * L * n) + cc;
+        for (int i0 = 16 * half; i0 < n; i0 += 32) {
             uint32_t va[16], vb[16];
             tmem_ld16(trow + (uint32_t)i0, va);
             tmem_ld16(trow + (uint32_t)(n + i0), vb);
@@ -322,9 +418,9 @@ __global__ void __launch_bounds__(128, 1) k_modeprod_tc(const __grid_constant__ 
                 const int i = i0 + j;
                 const float av = __uint_as_float(va[j]);
                 const float pb = __shfl_xor_sync(0xffffffffu, __uint_as_float(vb[j]), 1);
-                const float o = c == 0 ? av - pb : av + pb;
-                if (i < n && ll < lv) {
-                    const int64_t g = 2 * (l0 + ll + (int64_t)i * L + r * L * n) + c;
+                const float o = cc == 0 ? av - pb : av + pb;
+                if (i < n && live) {
+                    const int64_t g = base + 2 * (int64_t)i * L;
                     if (EPI == EPI_STORE) {
                         reinterpret_cast<float *>(a.out)[g] = o;
                     } else if (EPI == EPI_STORE_NORM) {
@@ -340,9 +436,49 @@ __global__ void __launch_bounds__(128, 1) k_modeprod_tc(const __grid_constant__ 
                 }
             }
         }
+    };
+
+    // pipeline: with two buffers the MMAs of tile t+1 run while tile t drains
+    // (`pending` is uniform across the block: MMAs issued and not yet waited for)
+    const int64_t G = gridDim.x;
+    int64_t tile = blockIdx.x;
+    bool pending[2] = {false, false};
+    if (tile < ntile && !s_fail) {
+        fetch(tile);
+        stage(0);
+        __syncthreads();
+        if (tid == 0) issue(0);
+        pending[0] = true;
+        if (tile + G < ntile) fetch(tile + G);
+    }
+    for (int it = 0; tile < ntile && !s_fail; tile += G, ++it) {
+        const int cur = nbuf == 2 ? (it & 1) : 0;
+        const int64_t next = tile + G;
+        if (nbuf == 2 && next < ntile) {
+            stage(cur ^ 1);
+            __syncthreads();
+            if (tid == 0) issue(cur ^ 1);
+            pending[cur ^ 1] = true;
+            if (next + G < ntile) fetch(next + G);
+        }
+        if (!mbar_wait(&mbar_mma[cur], phase[cur])) s_fail = 1;
+        phase[cur] ^= 1u;
+        pending[cur] = false;
+        tc_fence_after();
+        epilogue(tile, cur);
         tc_fence_before();
         __syncthreads();
+        if (nbuf == 1 && next < ntile && !s_fail) {
+            stage(0);
+            __syncthreads();
+            if (tid == 0) issue(0);
+            pending[0] = true;
+            if (next + G < ntile) fetch(next + G);
+        }
     }
+    // after a timeout: let MMAs still in flight finish before TMEM is released
+    for (int b = 0; b < 2; ++b)
+        if (pending[b] && !mbar_wait(&mbar_mma[b], phase[b])) s_fail = 1;
 
     if (EPI == EPI_STORE_NORM || EPI == EPI_ACCUM) {
         nd = warp_max(nd);
@@ -356,35 +492,45 @@ __global__ void __launch_bounds__(128, 1) k_modeprod_tc(const __grid_constant__ 
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 0) tmem_dealloc(tmem, (uint32_t)a.tmem_cols);
+    if (warp == 0) tmem_dealloc(tmem, (uint32_t)(a.tmem_cols * nbuf));
 }
 
 cudaError_t launch_modeprod_tc(int epi, const TCArgs &a, int grid, size_t smem, cudaStream_t st) {
     if (a.tilesL * a.R <= 0) return cudaSuccess;
+    if (a.mode1) {
+        // first-mode pass: never the last pass of a transform (complex64 out)
+        if (epi != EPI_STORE || (a.n & 7) || a.n > 80) return cudaErrorInvalidValue;
+        if (a.in_c128)
+            k_modeprod_tc<EPI_STORE, 1, 1><<<grid, TC_THREADS, smem, st>>>(a);
+        else
+            k_modeprod_tc<EPI_STORE, 1, 0><<<grid, TC_THREADS, smem, st>>>(a);
+        return cudaGetLastError();
+    }
+    if (a.in_c128) return cudaErrorInvalidValue;
     if (epi == EPI_STORE)
-        k_modeprod_tc<EPI_STORE><<<grid, 128, smem, st>>>(a);
+        k_modeprod_tc<EPI_STORE, 0, 0><<<grid, TC_THREADS, smem, st>>>(a);
     else if (epi == EPI_STORE_NORM)
-        k_modeprod_tc<EPI_STORE_NORM><<<grid, 128, smem, st>>>(a);
+        k_modeprod_tc<EPI_STORE_NORM, 0, 0><<<grid, TC_THREADS, smem, st>>>(a);
     else if (epi == EPI_ACCUM)
-        k_modeprod_tc<EPI_ACCUM><<<grid, 128, smem, st>>>(a);
+        k_modeprod_tc<EPI_ACCUM, 0, 0><<<grid, TC_THREADS, smem, st>>>(a);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 
+template <int EPI, int M1, int IN128>
+static cudaError_t tc_attr() {
+    return cudaFuncSetAttribute(k_modeprod_tc<EPI, M1, IN128>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_MAX);
+}
+
 cudaError_t modeprod_tc_init_attrs() {
     cudaError_t e;
-    const int bytes = 220 * 1024;   // below the 227 KB opt-in limit, leaving room for static smem
-    if ((e = cudaFuncSetAttribute(k_modeprod_tc<EPI_STORE>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) !=
-        cudaSuccess)
-        return e;
-    if ((e = cudaFuncSetAttribute(k_modeprod_tc<EPI_STORE_NORM>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) !=
-        cudaSuccess)
-        return e;
-    return cudaFuncSetAttribute(k_modeprod_tc<EPI_ACCUM>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if ((e = tc_attr<EPI_STORE, 0, 0>()) != cudaSuccess) return e;
+    if ((e = tc_attr<EPI_STORE_NORM, 0, 0>()) != cudaSuccess) return e;
+    if ((e = tc_attr<EPI_ACCUM, 0, 0>()) != cudaSuccess) return e;
+    if ((e = tc_attr<EPI_STORE, 1, 0>()) != cudaSuccess) return e;
+    return tc_attr<EPI_STORE, 1, 1>();
 }
 
 uint32_t tc_idesc(int M, int N) { return idesc_tf32(M, N); }

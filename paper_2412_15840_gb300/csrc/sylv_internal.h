@@ -116,16 +116,26 @@ struct DiagArgs {
     DevFlags *flags;
 };
 
+// dynamic shared memory of the tensor-core pass (below the 227 KB opt-in limit,
+// leaving room for its static shared memory)
+constexpr int TC_SMEM_MAX = 220 * 1024;
+
 // Tensor-core (tcgen05, 3xTF32) transform pass over one mode, complex64 in.
+// mode1 = 0: modes with L >= 64, a tile is 64 consecutive l of one r;
+// mode1 = 1: the first mode (L = 1), a tile is 64 consecutive columns r.
 struct TCArgs {
-    const float *in;              // complex64 tensor, interleaved floats
+    const void *in;               // complex64 tensor (complex128 allowed when mode1)
     void *out;                    // complex64, or complex128 for the last back pass
     const unsigned char *bimg;    // B_hi image followed by B_lo image (shared-memory layout)
     int n, Kp, Np;                // mode size, K padded to 8, N = 2n padded to 16
-    int sboA, sboB;               // 8-row group strides of the A and B operands (bytes)
+    int mode1;                    // 1: first-mode pass (L = 1)
+    int in_c128;                  // mode1 only: the input is complex128
+    int lboA, sboA, sboB;         // A: K-adjacent and 8-row-group strides; B: 8-row stride
+    int abytes;                   // bytes of one A image (hi or lo)
     int bimg_bytes;               // bytes of one B image
-    int tmem_cols;                // TMEM columns allocated (power of two >= 32)
-    int64_t L, R, tilesL;         // view (L, n, R); tiles of 64 l along L
+    int tmem_cols;                // TMEM columns of one accumulator (power of two >= 32)
+    int nbuf;                     // A operand / accumulator buffers (1 or 2)
+    int64_t L, R, tilesL;         // view (L, n, R); tiles of 64 along L (or R when mode1)
     DevFlags *flags;
     const int *done;
 };

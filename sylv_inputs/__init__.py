@@ -181,6 +181,6 @@ def manufactured(shape: Sequence[int], nrhs: int = 1, seed: int = 0,
 
 def initial_state(shape: Sequence[int], nrhs: int = 1, seed: int = 1) -> np.ndarray:
     """Initial value X(0) for the ODE X_t = sum_j A_j (x)_j X + B (Theorem 1):
-    a unit-variance complex Gaussian tensor from its own seeded stream."""
-    full = tuple(shape) + ((nrhs,) if nrhs > 1 else ())
-    return complex_gaussian(np.random.default_rng(seed), full)
+    a unit-variance complex Gaussian tensor from its own seeded stream, with
+    the trailing right-hand-side axis of Problem.B."""
+    return complex_gaussian(np.random.default_rng(seed), tuple(shape) + (nrhs,))

@@ -67,6 +67,8 @@ SHAPES = [
     ((70, 3), 1), ((9, 10, 11, 3), 1), ((100, 2, 2), 1),
     # modes longer than the largest automatic tile extent (64)
     ((600, 9), 1), ((130, 3, 2), 2),
+    # first mode on the tensor cores (n % 8 == 0, 32 <= n <= 80, >= 64 columns)
+    ((64, 70), 1), ((48, 5, 16), 2), ((80, 9, 8), 1), ((32, 32, 32), 1), ((40, 2, 33), 2),
 ]
 
 
@@ -133,7 +135,8 @@ def test_errors_are_reported():
 # ---------------------------------------------------------------- per phase --
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-@pytest.mark.parametrize("shape", [(8, 8, 8), (13, 1, 9, 4), (2, 2, 3, 2, 2)])
+@pytest.mark.parametrize("shape", [(8, 8, 8), (13, 1, 9, 4), (2, 2, 3, 2, 2), (64, 70),
+                                   (48, 5, 16), (40, 2, 33), (80, 9, 8)])
 def test_phases_with_the_plans_factors(shape, prec):
     p = si.random_problem(shape, 2, seed=len(shape))
     plan = Plan(A=p.A, nrhs=2, prec=prec)
