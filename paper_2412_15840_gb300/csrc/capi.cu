@@ -407,8 +407,10 @@ sylv_status build_sweep(const sylv_plan_s &p, const int *b, int threads, SweepCo
         a.tdoff[q] = td;
         td += a.b[a.inmode[q]] * a.b[a.inmode[q]];
     }
+    a.tdsize = td;
     cfg.threads = threads;
-    cfg.smem = (size_t)a.Pt * (esz + 16) + ((size_t)SWEEP_KCH * a.bmax + td) * esz;
+    cfg.smem = (size_t)a.Pt * (esz + 16) + ((size_t)SWEEP_KCH * a.bmax + td) * esz +
+               (a.fast ? (size_t)a.Pt * 12 : 0);     // packed coordinates + schedule
     if (cfg.smem > 200 * 1024) return SYLV_ERR_SHAPE;
 
     // device tables: order | sched | lev | sched_e | coord

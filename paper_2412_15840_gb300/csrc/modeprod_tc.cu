@@ -178,8 +178,9 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
 
 }  // namespace
 
-constexpr int TC_THREADS = 256;  // 8 warps: two per TMEM lane quadrant
-constexpr int TC_NU = 10;        // staging units per thread: 32 n / 256 <= 10 for n <= 80
+constexpr int TC_WARPS = 16;              // four per TMEM lane quadrant
+constexpr int TC_THREADS = 32 * TC_WARPS;
+constexpr int TC_NU = 5;                  // staging units per thread: 32 n / 512 <= 5 for n <= 80
 
 // byte offset of element (row, k) in a K-major, no-swizzle operand with
 // K-adjacent core matrices `lbo` bytes apart and 8-row groups `sbo` apart
@@ -279,7 +280,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_modeprod_tc(const __grid_cons
         const float *src = reinterpret_cast<const float *>(a.in) + 2 * (ll0 + rr * L * n);
 #pragma unroll
         for (int b = 0; b < TC_NU; ++b) {
-            const int u = warp + 8 * b;
+            const int u = warp + TC_WARPS * b;
             const int m4 = (u & 3) * 8 + (lane & 7);
             const int k = (u >> 2) * 4 + (lane >> 3);
             x[b][0] = x[b][1] = x[b][2] = x[b][3] = 0.f;
@@ -326,16 +327,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_modeprod_tc(const __grid_cons
                     make_float2(x[b][1] - h[1], x[b][3] - h[3]);
                 continue;
             }
-            const int u = warp + 8 * b;
+            const int u = warp + TC_WARPS * b;
             if (u >= Kp) continue;
             const int m4 = (u & 3) * 8 + (lane & 7);
             const int k = (u >> 2) * 4 + (lane >> 3);
+            // rows 4 m4 .. 4 m4 + 3 share an 8-row group: 16 bytes apart
+            const uint32_t off = kmaj_off2(4 * m4, k, lboA, sboA);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const float h = tf32_rna(x[b][j]);
-                const uint32_t off = kmaj_off2(4 * m4 + j, k, lboA, sboA);
-                *reinterpret_cast<float *>(Ahi + off) = h;
-                *reinterpret_cast<float *>(Alo + off) = x[b][j] - h;
+                *reinterpret_cast<float *>(Ahi + off + 16u * j) = h;
+                *reinterpret_cast<float *>(Alo + off + 16u * j) = x[b][j] - h;
             }
         }
         fence_proxy_async_smem();
@@ -360,8 +362,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_modeprod_tc(const __grid_cons
         mma_commit(&mbar_mma[buf]);
     };
     // TMEM lane m = 32 (warp & 3) + lane holds row (p, c) = (m / 2, m % 2) of the
-    // tile; the two warps of a lane quadrant take alternate 16-column chunks
-    const int q = warp & 3, half = warp >> 2;
+    // tile; the four warps of a lane quadrant take every fourth 16-column chunk
+    const int q = warp & 3, quarter = warp >> 2;
     const int m = 32 * q + lane;
     const int ll = m >> 1, cc = m & 1;
     auto epilogue = [&](int64_t t, int buf) {
@@ -372,7 +374,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_modeprod_tc(const __grid_cons
             const int64_t p0 = t * 64;
             const bool live = p0 + ll < a.R;
             float2 *orow = reinterpret_cast<float2 *>(a.out) + (p0 + ll) * n;
-            for (int i0 = 16 * half; i0 < n; i0 += 32) {
+            for (int i0 = 16 * quarter; i0 < n; i0 += 64) {
                 uint32_t va[16], vb[16];
                 tmem_ld16(trow + (uint32_t)i0, va);
                 tmem_ld16(trow + (uint32_t)(n + i0), vb);
@@ -403,35 +405,47 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_modeprod_tc(const __grid_cons
             }
             return;
         }
+        // complex out[l, i]: lane c of a pair stores the columns i0 + 2t + c
+        // (t < 8) after one exchange per column pair
         const int64_t r = t / a.tilesL;
         const int64_t l0 = (t % a.tilesL) * 64;
         const int lv = (int)((L - l0) < 64 ? (L - l0) : 64);
         const bool live = ll < lv;
-        const int64_t base = 2 * (l0 + ll + r * L * n) + cc;
-        for (int i0 = 16 * half; i0 < n; i0 += 32) {
+        const int64_t base = l0 + ll + r * L * n;            // complex index of (l, 0)
+        for (int i0 = 16 * quarter; i0 < n; i0 += 64) {
             uint32_t va[16], vb[16];
             tmem_ld16(trow + (uint32_t)i0, va);
             tmem_ld16(trow + (uint32_t)(n + i0), vb);
             tmem_wait_ld();
+            float o[16];
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-                const int i = i0 + j;
                 const float av = __uint_as_float(va[j]);
                 const float pb = __shfl_xor_sync(0xffffffffu, __uint_as_float(vb[j]), 1);
-                const float o = cc == 0 ? av - pb : av + pb;
+                o[j] = cc == 0 ? av - pb : av + pb;
+            }
+#pragma unroll
+            for (int t2 = 0; t2 < 8; ++t2) {
+                const float send = cc == 0 ? o[2 * t2 + 1] : o[2 * t2];
+                const float recv = __shfl_xor_sync(0xffffffffu, send, 1);
+                const float re = cc == 0 ? o[2 * t2] : recv;
+                const float im = cc == 0 ? recv : o[2 * t2 + 1];
+                const int i = i0 + 2 * t2 + cc;
                 if (i < n && live) {
-                    const int64_t g = base + 2 * (int64_t)i * L;
+                    const int64_t g = base + (int64_t)i * L;
                     if (EPI == EPI_STORE) {
-                        reinterpret_cast<float *>(a.out)[g] = o;
+                        reinterpret_cast<float2 *>(a.out)[g] = make_float2(re, im);
                     } else if (EPI == EPI_STORE_NORM) {
-                        reinterpret_cast<double *>(a.out)[g] = (double)o;
-                        nx = fmaxf(nx, fabsf(o));
+                        reinterpret_cast<double2 *>(a.out)[g] = make_double2(re, im);
+                        nx = fmaxf(nx, fmaxf(fabsf(re), fabsf(im)));
                     } else if (EPI == EPI_ACCUM) {
-                        double *xp = reinterpret_cast<double *>(a.out) + g;
-                        const double xn = *xp + (double)o;
-                        *xp = xn;
-                        nd = fmaxf(nd, fabsf(o));
-                        nx = fmaxf(nx, fabsf((float)xn));
+                        double2 *xp = reinterpret_cast<double2 *>(a.out) + g;
+                        double2 xv = *xp;
+                        xv.x += (double)re;
+                        xv.y += (double)im;
+                        *xp = xv;
+                        nd = fmaxf(nd, fmaxf(fabsf(re), fabsf(im)));
+                        nx = fmaxf(nx, fmaxf(fabsf((float)xv.x), fabsf((float)xv.y)));
                     }
                 }
             }

@@ -35,6 +35,10 @@ namespace sylv {
 
 constexpr int SW_KCH = SWEEP_KCH;
 constexpr int SW_RG = 8;     // fiber rows kept in registers at once
+// lanes sharing one entry in the in-tile wavefront: 4 on the FP32 path (whose
+// wavefront is latency-bound), 1 on the FP64 path (bound by the FP64 pipe)
+template <typename real> struct SwSub { static constexpr int value = 1; };
+template <> struct SwSub<float> { static constexpr int value = 4; };
 
 // The reciprocal of a diagonal sum is formed in FP64 in stage 1 and applied in
 // the in-tile wavefront: as double2 on the FP64 path; on the FP32 path as the
@@ -61,7 +65,7 @@ __device__ __forceinline__ float2 apply_inv(float2 n, float4 v) {
 }
 
 template <typename real>
-__global__ void __launch_bounds__(256) k_sweep(const __grid_constant__ SweepArgs a) {
+__global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 1) k_sweep(const __grid_constant__ SweepArgs a) {
     using C2 = typename C2T<real>::type;
     using Inv = typename InvT<real>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -69,6 +73,10 @@ __global__ void __launch_bounds__(256) k_sweep(const __grid_constant__ SweepArgs
     C2 *tile_s = reinterpret_cast<C2 *>(inv_s + a.Pt);
     C2 *Ts = tile_s + a.Pt;                       // SW_KCH x bmax block of T_j
     C2 *Td = Ts + SW_KCH * a.bmax;                // diagonal blocks of the in-tile modes
+    // full tiles: packed in-tile coordinates and the level schedule, copied
+    // once per CTA (every full tile uses the same tables)
+    unsigned long long *coord_s = reinterpret_cast<unsigned long long *>(Td + a.tdsize);
+    int *sched_s = reinterpret_cast<int *>(coord_s + (a.fast ? a.Pt : 0));
     __shared__ int s_ticket, s_tile, s_abort, s_full;
     __shared__ int64_t s_o[MAXM];
     __shared__ int s_be[MAXM], s_cnt[MAXM], s_I[MAXM];
@@ -78,6 +86,13 @@ __global__ void __launch_bounds__(256) k_sweep(const __grid_constant__ SweepArgs
     if (*(volatile const int *)&a.flags->done) return;
     C2 *Y = reinterpret_cast<C2 *>(a.Y);
     const int Nm = a.Nm, nin = a.nin, nt = blockDim.x;
+    if (a.fast) {
+        for (int e = threadIdx.x; e < a.Pt; e += nt) {
+            coord_s[e] = a.coord[e];
+            sched_s[e] = a.sched_e[e];
+        }
+        // (the first __syncthreads of the tile loop orders these stores)
+    }
 
     for (;;) {
         if (threadIdx.x == 0) {
@@ -156,7 +171,7 @@ __global__ void __launch_bounds__(256) k_sweep(const __grid_constant__ SweepArgs
             bool ok = true;
             double ex = s_den0x, ey = s_den0y;
             if (full) {
-                const unsigned long long c = a.coord[e];
+                const unsigned long long c = coord_s[e];
                 for (int q = 0; q < nin; ++q) {
                     const int j = a.inmode[q];
                     const int t = (int)((c >> (8 * q)) & 255u);
@@ -224,7 +239,7 @@ __global__ void __launch_bounds__(256) k_sweep(const __grid_constant__ SweepArgs
                     int64_t g0 = gbase;
                     bool ok = true;
                     if (full) {
-                        const unsigned long long c = a.coord[e0];
+                        const unsigned long long c = coord_s[e0];
                         for (int p = 0; p < nin; ++p)
                             g0 += (int64_t)((c >> (8 * p)) & 255u) * a.S[a.inmode[p]];
                     } else {
@@ -248,6 +263,23 @@ __global__ void __launch_bounds__(256) k_sweep(const __grid_constant__ SweepArgs
                         const C2 *yp = ybase;
                         const C2 *tc = Ts + rg;
                         int c = 0;
+                        // FP32: 8 strip loads in flight per thread (the loads are
+                        // latency-bound); FP64 keeps 4 (register budget)
+                        constexpr int UNR = sizeof(real) == 4 ? 8 : 4;
+                        for (; UNR == 8 && c + 8 <= ncol; c += 8) {
+                            C2 y[8];
+#pragma unroll
+                            for (int u = 0; u < 8; ++u) y[u] = __ldcg(yp + u * Sj);
+                            yp += 8 * Sj;
+#pragma unroll
+                            for (int r = 0; r < SW_RG; ++r) {
+                                if (rg + r < bej) {
+#pragma unroll
+                                    for (int u = 0; u < 8; ++u) cmsub(acc[r], tc[u * bj + r], y[u]);
+                                }
+                            }
+                            tc += 8 * bj;
+                        }
                         for (; c + 4 <= ncol; c += 4) {
                             const C2 y0 = __ldcg(yp), y1 = __ldcg(yp + Sj);
                             const C2 y2 = __ldcg(yp + 2 * Sj), y3 = __ldcg(yp + 3 * Sj);
@@ -285,45 +317,64 @@ __global__ void __launch_bounds__(256) k_sweep(const __grid_constant__ SweepArgs
             }
         }
 
-        // stage 2: in-tile wavefront over index sums measured from the tile's end
+        // stage 2: in-tile wavefront over index sums measured from the tile's end.
+        // SW_SUB consecutive lanes share an entry: lane `sub` sums the in-tile
+        // successors along in-tile modes sub, sub + SW_SUB, ...; the partial
+        // sums are combined with shuffles and lane 0 of the group divides.
+        constexpr int SW_SUB = SwSub<real>::value;
         for (int lev = 0; lev < a.Lin; ++lev) {
             const int q0 = a.lev_start[lev], q1 = a.lev_start[lev + 1];
-            for (int qq = q0 + threadIdx.x; qq < q1; qq += nt) {
+            for (int base = q0; base < q1; base += nt / SW_SUB) {
+                const int qq = base + (int)threadIdx.x / SW_SUB;
+                const int sub = (int)threadIdx.x % SW_SUB;
+                bool act = qq < q1;
                 int e = 0;
                 unsigned long long c = 0;
-                if (full) {
-                    e = a.sched_e[qq];
-                    c = a.coord[e];
-                } else {
-                    int r = a.sched[qq];
-                    bool ok = true;
-                    for (int p = 0; p < nin; ++p) {
+                if (act) {
+                    if (full) {
+                        e = sched_s[qq];
+                        c = coord_s[e];
+                    } else {
+                        int r = a.sched[qq];
+                        for (int p = 0; p < nin; ++p) {
+                            const int j = a.inmode[p];
+                            const int bj = a.b[j];
+                            const int apj = r % bj;
+                            r /= bj;
+                            if (apj >= s_be[j]) { act = false; break; }
+                            e += (s_be[j] - 1 - apj) * a.BS[p];
+                        }
+                    }
+                }
+                C2 part = czero<C2>();
+                if (act) {
+                    for (int p = sub; p < nin; p += SW_SUB) {
                         const int j = a.inmode[p];
+                        const int bs = a.BS[p];
+                        const int t = full ? (int)((c >> (8 * p)) & 255u) : (e / bs) % a.b[j];
+                        const int be = s_be[j];
+                        if (t + 1 >= be) continue;
                         const int bj = a.b[j];
-                        const int apj = r % bj;
-                        r /= bj;
-                        if (apj >= s_be[j]) { ok = false; break; }
-                        e += (s_be[j] - 1 - apj) * a.BS[p];
-                    }
-                    if (!ok) continue;
-                }
-                C2 num = tile_s[e];
-                for (int p = 0; p < nin; ++p) {
-                    const int j = a.inmode[p];
-                    const int bs = a.BS[p];
-                    const int t = full ? (int)((c >> (8 * p)) & 255u) : (e / bs) % a.b[j];
-                    const int be = s_be[j];
-                    if (t + 1 >= be) continue;
-                    const int bj = a.b[j];
-                    const C2 *tp = Td + a.tdoff[p] + t + (t + 1) * bj;
-                    const C2 *yp = tile_s + e + bs;
-                    for (int tt = t + 1; tt < be; ++tt) {     // in-tile successors
-                        cmsub(num, *tp, *yp);
-                        tp += bj;
-                        yp += bs;
+                        const C2 *tp = Td + a.tdoff[p] + t + (t + 1) * bj;
+                        const C2 *yp = tile_s + e + bs;
+                        for (int tt = t + 1; tt < be; ++tt) {     // in-tile successors
+                            cmsub(part, *tp, *yp);
+                            tp += bj;
+                            yp += bs;
+                        }
                     }
                 }
-                tile_s[e] = apply_inv(num, inv_s[e]);
+#pragma unroll
+                for (int o = 1; o < SW_SUB; o <<= 1) {
+                    part.x += __shfl_xor_sync(0xffffffffu, part.x, o);
+                    part.y += __shfl_xor_sync(0xffffffffu, part.y, o);
+                }
+                if (act && sub == 0) {
+                    C2 num = tile_s[e];
+                    num.x += part.x;
+                    num.y += part.y;
+                    tile_s[e] = apply_inv(num, inv_s[e]);
+                }
             }
             __syncthreads();
         }
@@ -333,7 +384,7 @@ __global__ void __launch_bounds__(256) k_sweep(const __grid_constant__ SweepArgs
             int64_t g = gbase;
             bool ok = true;
             if (full) {
-                const unsigned long long c = a.coord[e];
+                const unsigned long long c = coord_s[e];
                 for (int p = 0; p < nin; ++p)
                     g += (int64_t)((c >> (8 * p)) & 255u) * a.S[a.inmode[p]];
             } else {

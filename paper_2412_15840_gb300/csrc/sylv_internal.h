@@ -81,6 +81,7 @@ struct SweepArgs {
     int inmode[MAXM];         // indices of in-tile modes
     int BS[MAXM];             // box strides of in-tile modes (by position in inmode)
     int tdoff[MAXM];          // offset of each in-tile mode's b x b diagonal block of T
+    int tdsize;               // entries of all diagonal blocks
     int qpos[MAXM];           // position of mode j in inmode, or -1
     const void *T[MAXM];      // T_j, compute precision, column-major
     const double *d[MAXM];    // diag(T_j) as interleaved FP64 pairs
