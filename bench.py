@@ -481,6 +481,25 @@ def main():
     _, info_f = fp64.solve(B, X64, workspace=ws_f, stream=stream, info=True)
     X_fp64_host = from_device(X64, p.B.shape) if rank == 0 else None
 
+    # --- supplementary: the residual's products on the bf16 tensor cores
+    # (SYLV_MIXED_FP32_EMU; not the headline, which keeps the FP64 residual)
+    emu = Plan(A=p.A, nrhs=1, prec="mixed_emu", rtol=RTOL, max_refine=MAX_REFINE, device=local)
+    ws_e = emu.workspace()
+    Xe = torch.empty_like(B)
+
+    def step_emu():
+        emu.solve(B, Xe, workspace=ws_e, stream=stream)
+
+    for _ in range(args.warmup):
+        step_emu()
+    emu.set_timing(True)
+    ms_emu = timed(step_emu, args.steps, sampler)
+    emu.set_timing(False)
+    phases_e = emu.timing(reset=True)
+    _, info_e = emu.solve(B, Xe, workspace=ws_e, stream=stream, info=True)
+    X_emu_host = from_device(Xe, p.B.shape) if rank == 0 else None
+    del ws_e
+
     # --- end to end through the C ABI: pinned host B -> device, solve, X -> host
     X_host = torch.empty_like(B_host).pin_memory()
 
@@ -533,6 +552,14 @@ def main():
         "top_phase_mixed": top_phase,
         "setup_s": {"mixed": setup_s_mixed, "fp64": setup_s_fp64},
         "clocks": clocks,
+        "mixed_emu": {
+            "value": world * entries / (ms_emu * 1e-3), "unit": UNIT, "ms_per_step": ms_emu,
+            "residual": "mode products on the bf16 tensor cores (exact base-256 digit "
+                        "products, FP32-pair sums), not FP64",
+            "tensor_core_residual": bool(info_e["tensor_core_residual"]),
+            "refine_iters": info_e["refine_iters"],
+            "phases_ms_per_solve": {k: v / max(1, phases_e["solves"])
+                                    for k, v in phases_e["ms"].items()}},
     }
 
     if rank == 0 and not args.no_oracle:
@@ -542,6 +569,7 @@ def main():
         dt = time.perf_counter() - t0
         line["rel_err_vs_oracle"] = {"mixed": oracle.rel_err(X_mixed_host, Xo),
                                      "fp64": oracle.rel_err(X_fp64_host, Xo)}
+        line["mixed_emu"]["rel_err_vs_oracle"] = oracle.rel_err(X_emu_host, Xo)
         line["cpu_baseline"] = {
             "value": entries / dt, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
             "sample": "one full CPU-oracle solve of this rank-0 N=4, n=64 equation "

@@ -60,9 +60,19 @@ typedef enum {
 
 typedef enum {
     SYLV_FP64 = 0,        /* every phase in FP64 (complex128)                          */
-    SYLV_MIXED_FP32 = 1   /* forward / sweep / back in FP32 (complex64) with the FP64
+    SYLV_MIXED_FP32 = 1,  /* forward / sweep / back in FP32 (complex64) with the FP64
                              diagonal division, FP64 residual and FP64 update:
                              iterative refinement to relative error rtol            */
+    SYLV_MIXED_FP32_EMU = 2 /* as SYLV_MIXED_FP32, but the residual's mode products run
+                             on the bf16 tensor cores, exactly on 6 base-256 digits of
+                             X / 2^eX and A_j / 2^eA (Ozaki-style splitting), summed in
+                             FP32 pairs: the residual is accurate to ~2^-45 of
+                             sum_j ||A_j|| ||X|| instead of FP64 rounding.  Used when
+                             every non-singleton mode has 8 <= n_j <= 64, n_j % 8 == 0
+                             and tiles of 64 rows (prod_{m<j} n_m >= 64, or at least 64
+                             columns for the first mode); otherwise the residual stays
+                             FP64 (sylv_info.path bit 1 tells which ran).  Entries of
+                             B and of the scaled products must lie in the FP32 range. */
 } sylv_prec;
 
 /* Per-solve report, filled (after a stream synchronisation) only when the
@@ -72,7 +82,9 @@ typedef struct {
     int32_t refine_iters;     /* refinement steps taken (0 for SYLV_FP64)             */
     int32_t launches;         /* kernels this call enqueued                           */
     int32_t path;             /* bit 0: the sweep ran as the entrywise division of
-                                 Remark 1 (every A_j normal, see sylv_tuning)          */
+                                 Remark 1 (every A_j normal, see sylv_tuning);
+                                 bit 1: the residual ran on the tensor cores
+                                 (SYLV_MIXED_FP32_EMU)                                 */
     double last_corr_rel;     /* ||D_k|| / ||X_k|| of the last refinement step        */
     double est_rel_err;       /* contraction-based estimate of the final error        */
     double min_abs_den;       /* min |sum_j t_{j,i_j i_j}| over all multi-indices      */

@@ -20,7 +20,9 @@ LIB_PATH = os.path.join(_HERE, "libsylv.so")
 
 SYLV_FP64 = 0
 SYLV_MIXED_FP32 = 1
-PRECISIONS = {"fp64": SYLV_FP64, "mixed": SYLV_MIXED_FP32, "mixed_fp32": SYLV_MIXED_FP32}
+SYLV_MIXED_FP32_EMU = 2
+PRECISIONS = {"fp64": SYLV_FP64, "mixed": SYLV_MIXED_FP32, "mixed_fp32": SYLV_MIXED_FP32,
+              "mixed_emu": SYLV_MIXED_FP32_EMU}
 
 PHASES = ("forward", "sweep", "back", "residual", "update", "total", "evolve")
 
@@ -52,6 +54,7 @@ class Info(ctypes.Structure):
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
         d["diagonal_sweep"] = bool(self.path & 1)
+        d["tensor_core_residual"] = bool(self.path & 2)
         return d
 
 

@@ -140,6 +140,16 @@ struct sylv_plan_s {
 
     std::vector<Group> tgroups;   // transform passes in the working precision
     std::vector<Group> rgroups;   // FP64 residual passes
+    // SYLV_MIXED_FP32_EMU: residual passes on the bf16 tensor cores (one per mode)
+    struct OzPass {
+        int j = 0, mode1 = 0, n = 0, Kp = 0, Np = 0, lboX = 0, sboX = 0, sboAd = 0;
+        int ximg_bytes = 0, aimg_bytes = 0, tmem_cols = 0, eA = 0;
+        int64_t L = 1, R = 1, tilesL = 1;
+        size_t smem = 0;
+        const unsigned char *aimg = nullptr;
+    };
+    std::vector<OzPass> ozpasses;
+    bool oz = false;              // every mode qualifies: the residual runs on the tensor cores
 
     SweepConfig sweep;            // Y, T, diag, flags, counters filled per launch
     int64_t cnt_capacity = 0;     // tile counters the workspace holds (any tuned tiling)
@@ -182,6 +192,7 @@ struct sylv_plan_s {
     }
 
     bool fp64() const { return prec == SYLV_FP64; }
+    bool emu() const { return prec == SYLV_MIXED_FP32_EMU; }
 };
 
 namespace {
@@ -206,6 +217,51 @@ bool choose_tile(int64_t L, int64_t P, int64_t R, int64_t Et, int64_t Eh, int &L
     if (lt * P * rt > Eh) return false;
     Lt = (int)lt;
     Rt = (int)rt;
+    return true;
+}
+
+// Residual passes on the tensor cores: every non-singleton mode needs
+// 8 <= n <= 64, n % 8 == 0, and 64-row tiles (L >= 64, or >= 64 columns for
+// the first mode).  Returns false when some mode does not qualify.
+bool make_oz_passes(const sylv_plan_s &p, std::vector<sylv_plan_s::OzPass> &out) {
+    out.clear();
+    if (p.Nm == 0) return false;
+    const int64_t tot = p.ntot * p.nrhs;
+    for (int j = 0; j < p.Nm; ++j) {
+        const int64_t n = p.n[j], L = p.S[j];
+        if (n < 8 || n > 64 || n % 8) return false;
+        sylv_plan_s::OzPass o;
+        o.j = j;
+        o.n = (int)n;
+        o.mode1 = j == 0 ? 1 : 0;
+        o.L = L;
+        o.R = tot / (L * n);
+        if (o.mode1) {
+            if (o.R < 64) return false;
+        } else if (L < 64) {
+            return false;
+        }
+        o.tilesL = o.mode1 ? 1 : (L + 63) / 64;
+        o.Kp = (int)((n + 15) / 16 * 16);
+        o.Np = (int)((2 * n + 15) / 16 * 16);
+        if (o.mode1) {              // lanes along k: K-adjacent core matrices one padded column apart
+            o.sboX = 128;
+            o.lboX = 16 * 128 + 16;
+            o.ximg_bytes = (o.Kp / 8) * o.lboX;
+        } else {                    // lanes along l: padded 8-row groups
+            o.lboX = 128;
+            o.sboX = (o.Kp / 8) * 128 + 16;
+            o.ximg_bytes = 16 * o.sboX;
+        }
+        o.sboAd = (o.Kp / 8) * 128;
+        o.aimg_bytes = (o.Np / 8) * o.sboAd;
+        int cols = 32;
+        while (cols < 4 * o.Np) cols *= 2;
+        o.tmem_cols = cols;
+        o.smem = (size_t)6 * o.aimg_bytes + (size_t)6 * o.ximg_bytes + 4096;
+        if (o.smem > (size_t)TC_SMEM_MAX) return false;
+        out.push_back(o);
+    }
     return true;
 }
 
@@ -586,6 +642,37 @@ cudaError_t run_residual(Ctx &c, const void *B, const void *X, void *R, const in
     return cudaSuccess;
 }
 
+// R = B - sum_j A_j (x)_j X (sigma folded into the first mode) on the tensor
+// cores: FP32-pair R in `Rdf` between passes, complex64 R into `Rc64` at the end
+cudaError_t run_residual_oz(Ctx &c, const void *B, const void *X, void *Rdf, void *Rc64,
+                            const int *done) {
+    sylv_plan_s *p = c.p;
+    const size_t np = p->ozpasses.size();
+    for (size_t k = 0; k < np; ++k) {
+        const auto &o = p->ozpasses[k];
+        OzArgs a{};
+        a.X = X;
+        a.B = B;
+        a.Rin = Rdf;
+        a.Rout = Rdf;
+        a.Rc64 = Rc64;
+        a.aimg = o.aimg;
+        a.n = o.n; a.Kp = o.Kp; a.Np = o.Np; a.mode1 = o.mode1;
+        a.lboX = o.lboX; a.sboX = o.sboX; a.sboAd = o.sboAd;
+        a.ximg_bytes = o.ximg_bytes; a.aimg_bytes = o.aimg_bytes;
+        a.tmem_cols = o.tmem_cols; a.eA = o.eA;
+        a.L = o.L; a.R = o.R; a.tilesL = o.tilesL;
+        a.flags = c.flags;
+        a.done = done;
+        const int64_t tiles = o.mode1 ? (o.R + 63) / 64 : o.tilesL * o.R;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, p->num_sms));
+        cudaError_t e = launch_resid_oz(a, k == 0, k + 1 == np, grid, o.smem, c.st);
+        if (e != cudaSuccess) return e;
+        count(c);
+    }
+    return cudaSuccess;
+}
+
 cudaError_t run_sweep_cfg(Ctx &c, const SweepConfig &cfg, void *Y, bool fp64) {
     sylv_plan_s *p = c.p;
     SweepArgs a = cfg.a;
@@ -637,7 +724,7 @@ sylv_status fill_info(sylv_plan_s *p, DevFlags *flags, cudaStream_t st, sylv_inf
     info->status = s;
     info->refine_iters = p->fp64() ? 0 : h.iters;
     info->launches = launches;
-    info->path = p->diag_sweep ? 1 : 0;
+    info->path = (p->diag_sweep ? 1 : 0) | (p->oz ? 2 : 0);
     info->last_corr_rel = p->fp64() ? 0.0 : (double)h.lastcorr;
     info->est_rel_err = p->fp64() ? 0.0 : (double)h.est;
     info->min_abs_den = p->min_den;
@@ -698,11 +785,18 @@ sylv_status solve_impl(sylv_plan_s *p, const void *B, void *X, void *ws, cudaStr
         phase_end(c);
         for (int it = 1; it <= p->max_refine; ++it) {
             phase_begin(c, SYLV_PH_RESIDUAL);
-            if (run_residual(c, B, X, R, done) != cudaSuccess) return SYLV_ERR_CUDA;
+            if (p->oz) {
+                // tensor-core residual: complex64 R straight into W
+                if (run_residual_oz(c, B, X, R, W, done) != cudaSuccess) return SYLV_ERR_CUDA;
+            } else if (run_residual(c, B, X, R, done) != cudaSuccess) {
+                return SYLV_ERR_CUDA;
+            }
             phase_end(c);
             phase_begin(c, SYLV_PH_FORWARD);
-            if (run_groups(c, p->tgroups, false, 0, R, ELEM_C128, W, ELEM_C64, W, ELEM_C64,
-                           EPI_STORE, done) != cudaSuccess)
+            if (p->oz ? run_groups(c, p->tgroups, false, 0, W, ELEM_C64, W, ELEM_C64, W, ELEM_C64,
+                                   EPI_STORE, done) != cudaSuccess
+                      : run_groups(c, p->tgroups, false, 0, R, ELEM_C128, W, ELEM_C64, W, ELEM_C64,
+                                   EPI_STORE, done) != cudaSuccess)
                 return SYLV_ERR_CUDA;
             phase_end(c);
             phase_begin(c, SYLV_PH_SWEEP);
@@ -886,10 +980,11 @@ sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t 
     if (!out) return SYLV_ERR_INVALID_ARG;
     *out = nullptr;
     if (!n || N < 1 || N > 256 || nrhs < 1) return SYLV_ERR_SHAPE;
-    if (prec != SYLV_FP64 && prec != SYLV_MIXED_FP32) return SYLV_ERR_INVALID_ARG;
+    if (prec != SYLV_FP64 && prec != SYLV_MIXED_FP32 && prec != SYLV_MIXED_FP32_EMU)
+        return SYLV_ERR_INVALID_ARG;
     const bool haveA = A != nullptr, haveQT = (Q != nullptr && T != nullptr);
     if (haveA == haveQT) return SYLV_ERR_INVALID_ARG;
-    if (prec == SYLV_MIXED_FP32 && (!(rtol > 0.0) || max_refine < 1)) return SYLV_ERR_INVALID_ARG;
+    if (prec != SYLV_FP64 && (!(rtol > 0.0) || max_refine < 1)) return SYLV_ERR_INVALID_ARG;
     sylv_plan_s *p = nullptr;
     try {
         p = new sylv_plan_s();
@@ -1025,6 +1120,7 @@ sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t 
     if (s != SYLV_OK) return s;
     s = make_groups(*p, true, false, gmax, false, p->rgroups);
     if (s != SYLV_OK) return s;
+    if (p->emu()) p->oz = make_oz_passes(*p, p->ozpasses);
     if (p->fp64()) {
         p->egroups = p->tgroups;
     } else {
@@ -1043,6 +1139,9 @@ sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t 
         reserve(nn * 16); reserve(nn * 16);              // -A_j, exp(t A_j)
     }
     reserve(3 * sizeof(unsigned long long));
+    const size_t oz_first = offs.size();
+    if (p->oz)
+        for (auto &o : p->ozpasses) reserve((size_t)6 * o.aimg_bytes);
     const size_t diag_idx = offs.size();
     if (p->diag_sweep) reserve((size_t)diag_P1 * 16);
     const size_t tc_first = offs.size();
@@ -1142,6 +1241,41 @@ sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t 
                 g.img[dir] = (const unsigned char *)(base + offs[ti + dir]);
             }
             ti += 2;
+        }
+    }
+    // residual digit images: [Re A^T | Im A^T] of A_j (A_1 + sigma I for the
+    // first mode) as 6 base-256 digits of |a| / 2^eA, bf16, K-major layout
+    if (p->oz) {
+        size_t oi2 = oz_first;
+        for (auto &o : p->ozpasses) {
+            const int j = o.j, n = o.n;
+            std::vector<cd> Am(p->Ah[p->orig[j]]);
+            if (j == 0)
+                for (int i = 0; i < n; ++i) Am[(size_t)(i + i * n)] += p->sigma;
+            double amax = 0.0;
+            for (auto &z : Am) amax = std::max(amax, std::max(std::fabs(z.real()), std::fabs(z.imag())));
+            o.eA = amax > 0.0 ? std::ilogb(amax) + 2 : 0;
+            unsigned char *img = reinterpret_cast<unsigned char *>(host.data()) + offs[oi2];
+            for (int ii = 0; ii < 2 * n; ++ii)
+                for (int k = 0; k < n; ++k) {
+                    const int i = ii < n ? ii : ii - n;
+                    const cd z = Am[(size_t)(i + k * n)];
+                    const double v = ii < n ? z.real() : z.imag();
+                    const uint64_t F = (uint64_t)std::floor(std::ldexp(std::fabs(v), 48 - o.eA));
+                    const size_t off = (size_t)(ii / 8) * o.sboAd + (size_t)(k / 8) * 128 +
+                                       (size_t)(ii % 8) * 16 + (size_t)(k % 8) * 2;
+                    for (int u = 0; u < 6; ++u) {
+                        const uint32_t d = (uint32_t)(F >> (40 - 8 * u)) & 0xFFu;
+                        const float fd = (float)d;
+                        uint32_t fb;
+                        std::memcpy(&fb, &fd, 4);
+                        uint16_t b = (uint16_t)(fb >> 16);        // exact: d has <= 8 bits
+                        if (d && v < 0) b |= 0x8000u;
+                        std::memcpy(img + (size_t)u * o.aimg_bytes + off, &b, 2);
+                    }
+                }
+            o.aimg = (const unsigned char *)(base + offs[oi2]);
+            ++oi2;
         }
     }
     // diagonal-sweep head table: sigma + sum of t_{j,i_j i_j} over the head modes

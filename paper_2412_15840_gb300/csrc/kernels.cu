@@ -270,6 +270,7 @@ __global__ void k_solve_init(DevFlags *f) {
         f->dprev = 0.f;
         f->est = 0.f;
         f->lastcorr = 0.f;
+        f->xlast = 0;
     }
 }
 
@@ -278,6 +279,7 @@ __global__ void k_refine_decide(DevFlags *f, float rtol, int step, int max_refin
     if (threadIdx.x != 0 || f->done) return;
     float dmax = __uint_as_float(f->dmax);
     float xmax = __uint_as_float(f->xmax);
+    f->xlast = f->xmax;
     if (step == 0) {
         f->dprev = xmax;
         f->dmax = 0;
@@ -375,6 +377,7 @@ cudaError_t kernels_init(int) {
     if ((e = set_smem_attr<float, float2, double2, EPI_STORE_NORM>()) != cudaSuccess) return e;
     if ((e = set_smem_attr<float, float2, double2, EPI_ACCUM>()) != cudaSuccess) return e;
     if ((e = modeprod_tc_init_attrs()) != cudaSuccess) return e;
+    if ((e = resid_oz_init_attrs()) != cudaSuccess) return e;
     return sweep_init_attrs();
 }
 

@@ -34,7 +34,8 @@ struct DevFlags {
     float dprev;     // ||D_{k-1}|| (||X_0|| before the first step)
     float est;       // estimated relative error after the last step
     float lastcorr;  // ||D_k|| / ||X_k||
-    int pad[7];
+    unsigned xlast;  // float bits: max(|re|,|im|) of the current X (scale of the residual)
+    int pad[6];
 };
 static_assert(sizeof(DevFlags) == 64, "DevFlags layout");
 
@@ -141,7 +142,30 @@ struct TCArgs {
     const int *done;
 };
 
+// Residual pass on the bf16 tensor cores (digit splitting, see resid_oz.cu).
+struct OzArgs {
+    const void *X;                // complex128
+    const void *B;                // complex128 (first pass)
+    const void *Rin;              // R as FP32 pairs (re hi, im hi, re lo, im lo), later passes
+    void *Rout;                   // the same, all passes but the last
+    void *Rc64;                   // R rounded to complex64, last pass
+    const unsigned char *aimg;    // 6 digit images of [Re A^T | Im A^T] (B operand layout)
+    int n, Kp, Np;                // mode size, K padded to 16, N = 2n padded to 16
+    int mode1;                    // 1: first mode (tiles of 64 columns)
+    int lboX, sboX;               // X digit images: K-adjacent / 8-row-group strides (bytes)
+    int sboAd;                    // A digit images: 8-row-group stride (bytes)
+    int ximg_bytes, aimg_bytes;   // bytes of one digit image
+    int tmem_cols;                // 4 accumulators of Np columns, power of two
+    int eA;                       // |A entries| < 2^(eA - 1)
+    int64_t L, R, tilesL;
+    DevFlags *flags;
+    const int *done;
+};
+
 #ifdef __CUDACC__
+cudaError_t launch_resid_oz(const OzArgs &a, int first, int last, int grid, size_t smem,
+                            cudaStream_t st);
+cudaError_t resid_oz_init_attrs();
 cudaError_t launch_modeprod_tc(int epi, const TCArgs &a, int grid, size_t smem, cudaStream_t st);
 cudaError_t modeprod_tc_init_attrs();
 cudaError_t launch_modeprod(int fp64, int in_kind, int out_kind, int epi, const MPArgs &a,
