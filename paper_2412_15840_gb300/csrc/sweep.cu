@@ -35,8 +35,9 @@ namespace sylv {
 
 constexpr int SW_KCH = SWEEP_KCH;
 constexpr int SW_RG = 8;     // fiber rows kept in registers at once
-// lanes sharing one entry in the in-tile wavefront: 4 on the FP32 path (whose
-// wavefront is latency-bound), 1 on the FP64 path (bound by the FP64 pipe)
+// lanes sharing one entry in the in-tile wavefront: 4 on the FP32 path with
+// packed coordinates (its wavefront is latency-bound), else 1 (the FP64 path is
+// bound by the FP64 pipe; tiles of many small modes gain nothing)
 template <typename real> struct SwSub { static constexpr int value = 1; };
 template <> struct SwSub<float> { static constexpr int value = 4; };
 
@@ -65,7 +66,7 @@ __device__ __forceinline__ float2 apply_inv(float2 n, float4 v) {
 }
 
 template <typename real>
-__global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 1) k_sweep(const __grid_constant__ SweepArgs a) {
+__global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const __grid_constant__ SweepArgs a) {
     using C2 = typename C2T<real>::type;
     using Inv = typename InvT<real>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -321,7 +322,7 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 1) k_sweep(const 
         // SW_SUB consecutive lanes share an entry: lane `sub` sums the in-tile
         // successors along in-tile modes sub, sub + SW_SUB, ...; the partial
         // sums are combined with shuffles and lane 0 of the group divides.
-        constexpr int SW_SUB = SwSub<real>::value;
+        const int SW_SUB = a.fast ? SwSub<real>::value : 1;
         for (int lev = 0; lev < a.Lin; ++lev) {
             const int q0 = a.lev_start[lev], q1 = a.lev_start[lev + 1];
             for (int base = q0; base < q1; base += nt / SW_SUB) {
@@ -364,7 +365,6 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 1) k_sweep(const 
                         }
                     }
                 }
-#pragma unroll
                 for (int o = 1; o < SW_SUB; o <<= 1) {
                     part.x += __shfl_xor_sync(0xffffffffu, part.x, o);
                     part.y += __shfl_xor_sync(0xffffffffu, part.y, o);
