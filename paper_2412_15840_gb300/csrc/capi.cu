@@ -143,7 +143,7 @@ struct sylv_plan_s {
     // SYLV_MIXED_FP32_EMU: residual passes on the bf16 tensor cores (one per mode)
     struct OzPass {
         int j = 0, mode1 = 0, n = 0, Kp = 0, Np = 0, lboX = 0, sboX = 0, sboAd = 0;
-        int ximg_bytes = 0, aimg_bytes = 0, tmem_cols = 0, eA = 0;
+        int ximg_bytes = 0, aimg_bytes = 0, tmem_cols = 0, eA = 0, rstage_off = 0;
         int64_t L = 1, R = 1, tilesL = 1;
         size_t smem = 0;
         const unsigned char *aimg = nullptr;
@@ -258,7 +258,16 @@ bool make_oz_passes(const sylv_plan_s &p, std::vector<sylv_plan_s::OzPass> &out)
         int cols = 32;
         while (cols < 4 * o.Np) cols *= 2;
         o.tmem_cols = cols;
-        o.smem = (size_t)6 * o.aimg_bytes + (size_t)6 * o.ximg_bytes + 4096;
+        // epilogue operand slots (4 per 32 columns, 16 B per thread and slot): in
+        // the X digit images, free while the epilogue runs, or appended
+        const size_t rstage = (size_t)4 * ((n + 31) / 32) * 512 * 16;
+        const size_t xarea = (size_t)6 * o.ximg_bytes;
+        o.rstage_off = 6 * o.aimg_bytes;
+        o.smem = (size_t)6 * o.aimg_bytes + xarea + 4096;
+        if (rstage > xarea) {
+            o.rstage_off = (int)(o.smem);
+            o.smem += rstage;
+        }
         if (o.smem > (size_t)TC_SMEM_MAX) return false;
         out.push_back(o);
     }
@@ -660,6 +669,7 @@ cudaError_t run_residual_oz(Ctx &c, const void *B, const void *X, void *Rdf, voi
         a.n = o.n; a.Kp = o.Kp; a.Np = o.Np; a.mode1 = o.mode1;
         a.lboX = o.lboX; a.sboX = o.sboX; a.sboAd = o.sboAd;
         a.ximg_bytes = o.ximg_bytes; a.aimg_bytes = o.aimg_bytes;
+        a.rstage_off = o.rstage_off;
         a.tmem_cols = o.tmem_cols; a.eA = o.eA;
         a.L = o.L; a.R = o.R; a.tilesL = o.tilesL;
         a.flags = c.flags;

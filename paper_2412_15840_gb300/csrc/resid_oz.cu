@@ -92,6 +92,15 @@ __device__ __forceinline__ void split_double(double x, float &hi, float &lo) {
     lo = l;
 }
 
+// 16-byte asynchronous global -> shared copy (L2 only), per-thread completion
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 // FP32 pairs (hi, lo): error-free sum and the usual double-float addition
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
     s = a + b;
@@ -126,6 +135,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_resid_oz(const __grid_constan
     const int n = a.n, Kp = a.Kp, Np = a.Np;
     unsigned char *Aimg = sm;                                  // 6 digit images of A
     unsigned char *Ximg = sm + 6 * a.aimg_bytes;               // 6 digit images of X
+    // epilogue operands (R pairs or B), fetched once the MMAs no longer read the
+    // X digits: slot-major, 16 bytes per thread and slot
+    unsigned char *Rs = sm + a.rstage_off;
     const uint32_t lboX = (uint32_t)a.lboX, sboX = (uint32_t)a.sboX;
 
     if (tid == 0) {
@@ -198,6 +210,14 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_resid_oz(const __grid_constan
         }
     };
     auto stage = [&]() {
+        // K padding (k >= n) of every digit image: zero (the epilogue's staging
+        // area may have overwritten it)
+        for (int w = tid; w < 6 * 128 * (Kp - n); w += OZ_THREADS) {
+            const int img = w / (128 * (Kp - n)), rem = w - img * 128 * (Kp - n);
+            const int row = rem & 127, k = n + (rem >> 7);
+            *reinterpret_cast<uint16_t *>(Ximg + img * a.ximg_bytes +
+                                          kmaj_off_b16(row, k, lboX, sboX)) = 0;
+        }
 #pragma unroll
         for (int b = 0; b < OZ_EL; ++b) {
             const int e = tid + OZ_THREADS * b;
@@ -252,6 +272,20 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_resid_oz(const __grid_constan
         tile_base(t, r, p0, pv);
         const bool live = pl < pv;
         const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16);
+        // the values this lane updates: slot 4 c + t2 holds column 8 quarter + 32 c + 2 t2 + cc
+        {
+            int slot = 0;
+            for (int i0 = 8 * quarter; i0 < n; i0 += 32)
+                for (int t2 = 0; t2 < 4; ++t2, ++slot) {
+                    const int i = i0 + 2 * t2 + cc;
+                    if (!live || i >= n) continue;
+                    const int64_t g = gidx(r, p0, pl, i);
+                    const void *src = FIRST ? (const void *)(Bg + g) : (const void *)(Rin + g);
+                    cp_async16(Rs + ((size_t)slot * OZ_THREADS + tid) * 16, src);
+                }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        }
+        int slot = 0;
         for (int i0 = 8 * quarter; i0 < n; i0 += 32) {
             float sh[8], sl[8];
 #pragma unroll
@@ -273,9 +307,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_resid_oz(const __grid_constan
                     df_add(sh[j], sl[j], vh, vlo);
                 }
             }
+            cp_async_wait_all();
             // lane c keeps columns i0 + 2 t2 + c: exchange halves of the pairs
 #pragma unroll
-            for (int t2 = 0; t2 < 4; ++t2) {
+            for (int t2 = 0; t2 < 4; ++t2, ++slot) {
                 const int j0 = 2 * t2, j1 = 2 * t2 + 1;
                 const float send_h = cc == 0 ? sh[j1] : sh[j0];
                 const float send_l = cc == 0 ? sl[j1] : sl[j0];
@@ -289,10 +324,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_resid_oz(const __grid_constan
                 const int i = i0 + 2 * t2 + cc;
                 if (!live || i >= n) continue;
                 const int64_t g = gidx(r, p0, pl, i);
+                const unsigned char *sv = Rs + ((size_t)slot * OZ_THREADS + tid) * 16;
                 if (FIRST) {
                     // R = B - A (x) X in FP32 pairs (sigma is folded into the first
                     // mode's digits of A)
-                    const double2 bv = __ldcs(Bg + g);
+                    const double2 bv = *reinterpret_cast<const double2 *>(sv);
                     float xr, lr, xi, li;
                     split_double(bv.x, xr, lr);
                     split_double(bv.y, xi, li);
@@ -301,7 +337,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_resid_oz(const __grid_constan
                     if (LAST) Rc64[g] = make_float2(xr + lr, xi + li);
                     else Rout[g] = make_float4(xr, xi, lr, li);
                 } else {
-                    const float4 rv = Rin[g];
+                    const float4 rv = *reinterpret_cast<const float4 *>(sv);
                     float xr = rv.x, lr = rv.z, xi = rv.y, li = rv.w;
                     df_add(xr, lr, -reh, -rel);
                     df_add(xi, li, -imh, -iml);

@@ -155,6 +155,7 @@ struct OzArgs {
     int lboX, sboX;               // X digit images: K-adjacent / 8-row-group strides (bytes)
     int sboAd;                    // A digit images: 8-row-group stride (bytes)
     int ximg_bytes, aimg_bytes;   // bytes of one digit image
+    int rstage_off;               // shared-memory offset of the epilogue's operand slots
     int tmem_cols;                // 4 accumulators of Np columns, power of two
     int eA;                       // |A entries| < 2^(eA - 1)
     int64_t L, R, tilesL;
