@@ -26,8 +26,10 @@
  *    cudaStream_t passed as void*; NULL = legacy default stream) and
  *    asynchronous unless stated.  No entry point throws; every failure is a
  *    sylv_status.  CUDA errors map to SYLV_ERR_CUDA.
- *  - The library allocates only small per-plan device buffers (the factors
- *    and tiling tables) inside sylv_plan_create.  Tensor-sized scratch memory
+ *  - The library allocates device memory only inside sylv_plan_create: the
+ *    factors and tiling tables, and, when prod_j n_j * 16 bytes <= 1 GiB, a
+ *    table of the sweep's FP64 reciprocals (one per multi-index; without it
+ *    the sweep forms them on the fly).  Tensor-sized scratch memory
  *    is the caller's: query sylv_workspace_size and pass a device buffer of at
  *    least that many bytes, 256-byte aligned.
  *  - A plan may be used by one stream at a time: calls that overlap on the

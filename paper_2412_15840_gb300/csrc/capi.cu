@@ -154,6 +154,7 @@ struct sylv_plan_s {
     SweepConfig sweep;            // Y, T, diag, flags, counters filled per launch
     int64_t cnt_capacity = 0;     // tile counters the workspace holds (any tuned tiling)
     double den_scale = 1.0;       // power of two for the sweep's reciprocals
+    void *inv_tab = nullptr;      // reciprocal per multi-index (when within INV_TABLE_MAX)
     int num_sms = 1;
     long long timeout_cycles = 4000000000LL;   // per dependency wait
     int fault_tile = -1;                       // test hook (sylv_tuning.fault_tile - 1)
@@ -188,6 +189,7 @@ struct sylv_plan_s {
         for (auto e : ev_free) cudaEventDestroy(e);
         if (dpool) cudaFree(dpool);
         if (sweep.dbuf) cudaFree(sweep.dbuf);
+        if (inv_tab) cudaFree(inv_tab);
         if (cur >= 0 && cur != device) cudaSetDevice(cur);
     }
 
@@ -692,6 +694,7 @@ cudaError_t run_sweep_cfg(Ctx &c, const SweepConfig &cfg, void *Y, bool fp64) {
         a.d[j] = p->d64[j];
     }
     a.den_scale = p->den_scale;
+    a.inv_tab = p->inv_tab;
     a.cnt = c.cnt;
     a.flags = c.flags;
     cudaError_t e = launch_sweep_init(a, c.st);
@@ -1331,6 +1334,24 @@ sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t 
     // power of two centring |scale * sum|^2 on 1 for the sweep's reciprocals
     p->den_scale = std::ldexp(1.0, -(int)std::lround(0.5 * (std::log2(mn) + std::log2(mx))));
     p->diag.den_scale = p->den_scale;
+    // the sweep's reciprocals, once per plan, when the table stays within budget
+    if (!p->diag_sweep && p->Nm > 0 && (size_t)p->ntot * 16 <= INV_TABLE_MAX) {
+        if (cudaMalloc(&p->inv_tab, (size_t)p->ntot * 16) != cudaSuccess) {
+            cudaGetLastError();
+            p->inv_tab = nullptr;            // fall back to forming them in the sweep
+        } else {
+            SweepArgs ta{};
+            ta.Nm = p->Nm;
+            for (int j = 0; j < p->Nm; ++j) { ta.n[j] = p->n[j]; ta.d[j] = p->d64[j]; }
+            ta.sig_re = p->sigma.real();
+            ta.sig_im = p->sigma.imag();
+            ta.ntot = p->ntot;
+            ta.den_scale = p->den_scale;
+            if (launch_inv_table(p->fp64(), ta, p->inv_tab, p->num_sms, 0) != cudaSuccess ||
+                cudaDeviceSynchronize() != cudaSuccess)
+                return SYLV_ERR_CUDA;
+        }
+    }
 
     // sweep: default tiles (FP64 256 entries x 128 threads, FP32 1024 x 256,
     // measured on GB300) or the caller's block extents

@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
     __shared__ int s_ticket, s_tile, s_abort, s_full;
     __shared__ int64_t s_o[MAXM];
     __shared__ int s_be[MAXM], s_cnt[MAXM], s_I[MAXM];
-    __shared__ int64_t s_gbase;
+    __shared__ int64_t s_gbase, s_rhs0;
     __shared__ double s_den0x, s_den0y;
 
     if (*(volatile const int *)&a.flags->done) return;
@@ -158,6 +158,7 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
                 }
             }
             s_gbase = gb;
+            s_rhs0 = rhs * a.ntot;
             s_den0x = dx;
             s_den0y = dy;
             s_full = full && a.fast;
@@ -177,9 +178,11 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
                     const int j = a.inmode[q];
                     const int t = (int)((c >> (8 * q)) & 255u);
                     g += (int64_t)t * a.S[j];
-                    const int64_t ij = s_o[j] + t;
-                    ex += a.d[j][2 * ij];
-                    ey += a.d[j][2 * ij + 1];
+                    if (!a.inv_tab) {
+                        const int64_t ij = s_o[j] + t;
+                        ex += a.d[j][2 * ij];
+                        ey += a.d[j][2 * ij + 1];
+                    }
                 }
             } else {
                 int r = e;
@@ -200,7 +203,10 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
                 continue;
             }
             tile_s[e] = __ldcg(Y + g);
-            store_inv(crecip_scaled(ex, ey, a.den_scale), inv_s[e]);
+            if (a.inv_tab)       // reciprocals formed once per plan (k_inv_table)
+                inv_s[e] = __ldg(reinterpret_cast<const Inv *>(a.inv_tab) + (g - s_rhs0));
+            else
+                store_inv(crecip_scaled(ex, ey, a.den_scale), inv_s[e]);
         }
         // diagonal blocks T_j[o_j + r, o_j + c] (r < c < be_j) of the in-tile modes
         for (int p = 0; p < nin; ++p) {
@@ -421,6 +427,41 @@ __global__ void k_sweep_init(const __grid_constant__ SweepArgs a) {
         }
         a.cnt[tile] = c;
     }
+}
+
+// Reciprocals 1 / (sigma + sum_j t_{j,i_j i_j}) of every multi-index, formed in
+// FP64 once per plan and stored in the sweep's format (double2 on the FP64
+// path, the FP32 pair hi/lo on the FP32 path); the sweep then reads them
+// instead of spending FP64 instructions on its critical path.
+template <typename real>
+__global__ void k_inv_table(const __grid_constant__ SweepArgs a, void *tab) {
+    using Inv = typename InvT<real>::type;
+    Inv *out = reinterpret_cast<Inv *>(tab);
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < a.ntot;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        double dx = a.sig_re, dy = a.sig_im;
+        int64_t rem = idx;
+        for (int j = 0; j < a.Nm; ++j) {
+            const int64_t i = rem % a.n[j];
+            rem /= a.n[j];
+            dx += a.d[j][2 * i];
+            dy += a.d[j][2 * i + 1];
+        }
+        Inv v;
+        store_inv(crecip_scaled(dx, dy, a.den_scale), v);
+        out[idx] = v;
+    }
+}
+
+cudaError_t launch_inv_table(int fp64, const SweepArgs &a, void *tab, int num_sms,
+                             cudaStream_t st) {
+    if (a.ntot <= 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((a.ntot + 255) / 256, (int64_t)num_sms * 16);
+    if (fp64)
+        k_inv_table<double><<<(unsigned)blocks, 256, 0, st>>>(a, tab);
+    else
+        k_inv_table<float><<<(unsigned)blocks, 256, 0, st>>>(a, tab);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_sweep(int fp64, const SweepArgs &a, int grid, int threads, size_t smem,

@@ -17,6 +17,7 @@ constexpr int MAXM = 40;   // modes with n_j > 1 (after singleton removal)
 constexpr int MAXG = 16;   // modes fused into one transform pass
 constexpr int MAX_N = 1024;
 constexpr int SWEEP_KCH = 64;  // columns of T_j staged per chunk by the sweep
+constexpr size_t INV_TABLE_MAX = (size_t)1 << 30;  // plan-resident reciprocal table budget
 constexpr int SWEEP_BMAX = 64; // automatic tile extents stay <= 64 per mode, so the
                                // tile's diagonal T blocks fit in shared memory
 
@@ -97,6 +98,7 @@ struct SweepArgs {
     const int *lev_start;     // Lin + 1 entries
     long long timeout_cycles;
     int fault_tile;           // test hook: this tile never releases its predecessors (-1: none)
+    const void *inv_tab;      // per multi-index reciprocals in the sweep's format, or null
 };
 
 // Sweep of a plan whose T_j are all diagonal (every A_j normal, Remark 1):
@@ -174,6 +176,8 @@ cudaError_t launch_modeprod(int fp64, int in_kind, int out_kind, int epi, const 
 cudaError_t launch_sweep(int fp64, const SweepArgs &a, int grid, int threads, size_t smem,
                          cudaStream_t st);
 cudaError_t launch_sweep_init(const SweepArgs &a, cudaStream_t st);
+cudaError_t launch_inv_table(int fp64, const SweepArgs &a, void *tab, int num_sms,
+                             cudaStream_t st);
 cudaError_t launch_sweep_diag(int fp64, const DiagArgs &a, int num_sms, cudaStream_t st);
 cudaError_t launch_solve_init(DevFlags *f, cudaStream_t st);
 cudaError_t launch_refine_decide(DevFlags *f, float rtol, int step, int max_refine,
