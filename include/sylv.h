@@ -123,7 +123,9 @@ typedef struct {
                                  Eq. (yi1i2iNdiag), computed in FP64 and ignoring the
                                  rounding-level off-diagonal entries; 1 = always run
                                  the triangular sweep of Eq. (yi1i2iN) */
-    int32_t reserved[2];
+    int32_t sweep_ctas_per_sm;  /* 0 = as many sweep CTAs per SM as fit; k > 0 caps it
+                                 (fewer CTAs shorten each tile's latency) */
+    int32_t reserved[1];
 } sylv_tuning;
 
 /*

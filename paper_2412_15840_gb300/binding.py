@@ -67,7 +67,8 @@ class Tuning(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int32 * 64), ("group_max", ctypes.c_int32),
                 ("sweep_threads", ctypes.c_int32), ("no_tensor_cores", ctypes.c_int32),
                 ("timeout_ms", ctypes.c_int32), ("fault_tile", ctypes.c_int32),
-                ("general_sweep", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("general_sweep", ctypes.c_int32), ("sweep_ctas_per_sm", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 1)]
 
 
 _LIB = None
@@ -207,7 +208,7 @@ class Plan:
                  rtol: float = 1e-10, max_refine: int = 5, device: int = 0,
                  block: Optional[Sequence[int]] = None, group_max: int = 0,
                  sweep_threads: int = 0, tensor_cores: bool = True, timeout_ms: int = 0,
-                 fault_tile: int = 0, general_sweep: bool = False):
+                 fault_tile: int = 0, general_sweep: bool = False, sweep_ctas_per_sm: int = 0):
         L = _lib()
         if (A is None) == (Q is None or T is None):
             raise ValueError("give A, or both Q and T")
@@ -230,7 +231,7 @@ class Plan:
         pT = ptrs(T) if T is not None else None
         tun = None
         if block is not None or group_max or sweep_threads or not tensor_cores or timeout_ms \
-                or fault_tile or general_sweep:
+                or fault_tile or general_sweep or sweep_ctas_per_sm:
             tun = Tuning()
             if block is not None:
                 for j, b in enumerate(block):
@@ -241,6 +242,7 @@ class Plan:
             tun.timeout_ms = int(timeout_ms)
             tun.fault_tile = int(fault_tile)
             tun.general_sweep = int(bool(general_sweep))
+            tun.sweep_ctas_per_sm = int(sweep_ctas_per_sm)
         h = vp()
         s = L.sylv_plan_create(ctypes.byref(h), self.N, n, self.nrhs, pA, pQ, pT, self.prec,
                                float(rtol), int(max_refine), int(device),

@@ -84,7 +84,7 @@ struct TimedPhase {
 // One sweep configuration: kernel arguments (tables in `dbuf`), launch shape.
 struct SweepConfig {
     SweepArgs a{};
-    int threads = 256, grid = 1;
+    int threads = 256, grid = 1, per_sm = 1;
     size_t smem = 0;
     void *dbuf = nullptr;
 };
@@ -367,7 +367,8 @@ int64_t tiles_for(const sylv_plan_s &p, const int *b) {
 
 // Host tables of one sweep configuration (tile extents b, `threads` per CTA),
 // uploaded into a device buffer of its own.
-sylv_status build_sweep(const sylv_plan_s &p, const int *b, int threads, SweepConfig &cfg) {
+sylv_status build_sweep(const sylv_plan_s &p, const int *b, int threads, SweepConfig &cfg,
+                        int ctas_per_sm = 0) {
     SweepArgs &a = cfg.a;
     a = SweepArgs{};
     a.Nm = p.Nm;
@@ -507,9 +508,13 @@ sylv_status build_sweep(const sylv_plan_s &p, const int *b, int threads, SweepCo
     a.sched_e = (const int *)(base + o_se);
     a.coord = (const unsigned long long *)(base + o_coord);
 
-    // persistent grid: every SM holds as many tiles as fit
+    // persistent grid: every SM holds as many tiles as fit, or the requested
+    // number (fewer CTAs per SM shorten each tile's latency on the dependency
+    // chain at the cost of tiles in flight)
     int per = sweep_blocks_per_sm(p.fp64(), cfg.threads, cfg.smem);
     if (per < 1) per = 1;
+    if (ctas_per_sm > 0 && ctas_per_sm < per) per = ctas_per_sm;
+    cfg.per_sm = per;
     cfg.grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)p.num_sms * per, a.ntiles));
     return SYLV_OK;
 }
@@ -1361,7 +1366,7 @@ sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t 
         int threads = p->fp64() ? 128 : 256;
         if (tuning && tuning->sweep_threads > 0)
             threads = std::min(256, (tuning->sweep_threads + 31) / 32 * 32);
-        s = build_sweep(*p, b, threads, p->sweep);
+        s = build_sweep(*p, b, threads, p->sweep, tuning ? tuning->sweep_ctas_per_sm : 0);
         if (s != SYLV_OK) return s;
         // tile counters for any tiling the autotuner may install (tiles >= 64 entries)
         p->cnt_capacity = p->sweep.a.ntiles;
@@ -1517,24 +1522,28 @@ sylv_status sylv_plan_autotune(sylv_plan_t p, void *Tdev, void *ws, size_t ws_by
         int b[MAXM];
         choose_blocks(*p, target, nullptr, b);
         if (tiles_for(*p, b) > p->cnt_capacity) continue;
-        for (int threads = 128; threads <= 256; threads *= 2) {
-            SweepConfig cand;
-            if (build_sweep(*p, b, threads, cand) != SYLV_OK) {
-                if (cand.dbuf) cudaFree(cand.dbuf);
-                continue;
-            }
-            float ms = 0.f;
-            if (!time_cfg(cand, ms)) {
-                ok = false;
-                cudaFree(cand.dbuf);
-                break;
-            }
-            if (ms < cur_ms) {
-                cudaFree(p->sweep.dbuf);
-                p->sweep = cand;
-                cur_ms = ms;
-            } else {
-                cudaFree(cand.dbuf);
+        for (int threads = 128; ok && threads <= 256; threads *= 2) {
+            int max_per = 0;
+            for (int per = 0; ok && (per == 0 || per < max_per); ++per) {
+                SweepConfig cand;
+                if (build_sweep(*p, b, threads, cand, per) != SYLV_OK) {
+                    if (cand.dbuf) cudaFree(cand.dbuf);
+                    break;
+                }
+                if (per == 0) max_per = cand.per_sm;   // per = 0: as many as fit
+                float ms = 0.f;
+                if (!time_cfg(cand, ms)) {
+                    ok = false;
+                    cudaFree(cand.dbuf);
+                    break;
+                }
+                if (ms < cur_ms) {
+                    cudaFree(p->sweep.dbuf);
+                    p->sweep = cand;
+                    cur_ms = ms;
+                } else {
+                    cudaFree(cand.dbuf);
+                }
             }
         }
     }

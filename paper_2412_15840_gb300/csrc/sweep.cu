@@ -241,15 +241,24 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
                     Ts[c * bj + r] = __ldg(Tj + (oj + r) + (kend + k0 + c) * nj);
                 }
                 __syncthreads();
-                for (int f = threadIdx.x; f < F; f += nt) {
+                // H consecutive lanes share a fiber when the box has fewer fibers
+                // than threads (FP32 path): each sums a contiguous share of the
+                // columns, and the partial sums meet by shuffles (fixed order)
+                int H = 1;
+                if (sizeof(real) == 4)
+                    while (2 * H <= 8 && 2 * H * F <= nt) H *= 2;    // a power of two
+                const int per = (kk + H - 1) / H;
+                const int h = (int)threadIdx.x % H;
+                for (int fb = 0; fb < F; fb += nt / H) {
+                    const int f = fb + (int)threadIdx.x / H;
                     const int e0 = (q >= 0) ? (f / bs) * (bs * bj) + (f % bs) : f;
                     int64_t g0 = gbase;
-                    bool ok = true;
-                    if (full) {
+                    bool ok = f < F;
+                    if (ok && full) {
                         const unsigned long long c = coord_s[e0];
                         for (int p = 0; p < nin; ++p)
                             g0 += (int64_t)((c >> (8 * p)) & 255u) * a.S[a.inmode[p]];
-                    } else {
+                    } else if (ok) {
                         int r = e0;
                         for (int p = 0; p < nin; ++p) {
                             const int jj = a.inmode[p];
@@ -260,15 +269,15 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
                             g0 += (int64_t)t * a.S[jj];
                         }
                     }
-                    if (!ok) continue;
-                    const C2 *ybase = Y + g0 + (kend + k0 - oj) * Sj;
-                    const int ncol = kk;
+                    const int c0 = min(kk, h * per), c1 = ok ? min(kk, c0 + per) : c0;
+                    const C2 *ybase = Y + g0 + (kend + k0 - oj + c0) * Sj;
+                    const int ncol = c1 - c0;
                     for (int rg = 0; rg < bej; rg += SW_RG) {
                         C2 acc[SW_RG];
 #pragma unroll
                         for (int r = 0; r < SW_RG; ++r) acc[r] = czero<C2>();
                         const C2 *yp = ybase;
-                        const C2 *tc = Ts + rg;
+                        const C2 *tc = Ts + rg + c0 * bj;
                         int c = 0;
                         // FP32: 8 strip loads in flight per thread (the loads are
                         // latency-bound); FP64 keeps 4 (register budget)
@@ -310,12 +319,21 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
                                 if (rg + r < bej) cmsub(acc[r], tc[r], y);
                             tc += bj;
                         }
+                        for (int o = 1; o < H; o <<= 1) {
 #pragma unroll
-                        for (int r = 0; r < SW_RG; ++r) {
-                            if (rg + r < bej) {
-                                C2 &v = tile_s[e0 + (rg + r) * bs];
-                                v.x += acc[r].x;
-                                v.y += acc[r].y;
+                            for (int r = 0; r < SW_RG; ++r) {
+                                acc[r].x += __shfl_xor_sync(0xffffffffu, acc[r].x, o);
+                                acc[r].y += __shfl_xor_sync(0xffffffffu, acc[r].y, o);
+                            }
+                        }
+                        if (ok && h == 0) {
+#pragma unroll
+                            for (int r = 0; r < SW_RG; ++r) {
+                                if (rg + r < bej) {
+                                    C2 &v = tile_s[e0 + (rg + r) * bs];
+                                    v.x += acc[r].x;
+                                    v.y += acc[r].y;
+                                }
                             }
                         }
                     }
