@@ -350,19 +350,26 @@ def evolve_workload(args, local: int) -> int:
     return 0
 
 
-def kernels_once(local: int) -> int:
+def kernels_once(local: int, small_n: bool = False) -> int:
     """One launch group of every hot-path kernel family, in this order:
     FP64 residual passes, FP32 forward passes (first mode and modes 2-4 on
     the tensor cores), FP32 sweep, FP32 back passes, FP64 forward passes,
     FP64 sweep, then one solve with the tensor-core residual (a short, fixed
-    launch sequence for ncu captures)."""
+    launch sequence for ncu captures).  With --workload n2_N29: the same
+    sequence (without the last solve) on the n = 2 operators at N = 25."""
     import torch
     from paper_2412_15840_gb300.build import build
     build()
     from paper_2412_15840_gb300 import Plan, to_device
     dev = torch.device(f"cuda:{local}")
     torch.cuda.set_device(dev)
-    p = si.random_problem(SHAPE, 1, seed=0, name="N4_n64")
+    if small_n:
+        # the small-n workload's operators at N = 25 (2^23 entries, modes 5 and 17
+        # singletons): the same kernels per entry as N = 29, few GB for ncu
+        shape = tuple(1 if j in (4, 16) else 2 for j in range(25))
+        p = si.random_problem(shape, 1, seed=0, shift=2.0, scale=1.0 / np.sqrt(2.0))
+    else:
+        p = si.random_problem(SHAPE, 1, seed=0, name="N4_n64")
     m = Plan(A=p.A, nrhs=1, prec="mixed", device=local)
     f = Plan(A=p.A, nrhs=1, prec="fp64", device=local)
     B = to_device(p.B, device=dev)
@@ -375,9 +382,10 @@ def kernels_once(local: int) -> int:
     m.back(W)
     f.forward(X)
     f.sweep(X)
-    # one solve with the tensor-core residual (k_resid_oz passes)
-    e = Plan(A=p.A, nrhs=1, prec="mixed_emu", device=local)
-    e.solve(B, torch.empty_like(B))
+    if not small_n:
+        # one solve with the tensor-core residual (k_resid_oz passes)
+        e = Plan(A=p.A, nrhs=1, prec="mixed_emu", device=local)
+        e.solve(B, torch.empty_like(B))
     torch.cuda.synchronize(dev)
     print("kernels-once ok")
     return 0
@@ -391,7 +399,7 @@ def main():
     if args.impl == "reference":
         return run_reference(args, rank, world)
     if args.kernels_once:
-        return kernels_once(local)
+        return kernels_once(local, small_n=args.workload == "n2_N29")
     if args.workload == "evolve_n64_N4":
         return evolve_workload(args, local)
     if args.workload != "n64_N4":
