@@ -70,9 +70,9 @@ typedef enum {
                              X / 2^eX and A_j / 2^eA (Ozaki-style splitting), summed in
                              FP32 pairs: the residual is accurate to ~2^-45 of
                              sum_j ||A_j|| ||X|| instead of FP64 rounding.  Used when
-                             every non-singleton mode has 8 <= n_j <= 64, n_j % 8 == 0
-                             and tiles of 64 rows (prod_{m<j} n_m >= 64, or at least 64
-                             columns for the first mode); otherwise the residual stays
+                             every non-singleton mode has 8 <= n_j <= 64 and either
+                             prod_{m<j} n_m >= 8 or (first mode) at least 64 columns
+                             (prod_{m>1} n_m times nrhs); otherwise the residual stays
                              FP64 (sylv_info.path bit 1 tells which ran).  Entries of
                              B and of the scaled products must lie in the FP32 range. */
 } sylv_prec;

@@ -36,9 +36,12 @@ struct Group {
     const unsigned char *img[2] = {nullptr, nullptr};
 };
 
-// A mode runs on the tensor cores when its tile holds 64 complex positions
-// along the preceding modes and the operands fit in shared memory.
-bool tc_mode_ok(int64_t L, int64_t n) { return L >= 64 && n >= 32 && n <= 80; }
+// A mode after the first runs on the tensor cores when its fibres are at least
+// 8 positions apart (tiles of 64 rows of the flattened (l, r) index stay
+// mostly contiguous) and the operands fit in shared memory.
+bool tc_mode_ok(int64_t L, int64_t n) {
+    return L >= 8 && L < ((int64_t)1 << 30) && n >= 32 && n <= 80;
+}
 // The first mode (contiguous fibres) runs on the tensor cores with tiles of 64
 // columns when it is not the last pass of a transform and n is a multiple of 8.
 bool tc_mode1_ok(int64_t n, int64_t cols, int Nm) {
@@ -223,15 +226,16 @@ bool choose_tile(int64_t L, int64_t P, int64_t R, int64_t Et, int64_t Eh, int &L
 }
 
 // Residual passes on the tensor cores: every non-singleton mode needs
-// 8 <= n <= 64, n % 8 == 0, and 64-row tiles (L >= 64, or >= 64 columns for
-// the first mode).  Returns false when some mode does not qualify.
+// 8 <= n <= 64, and fibres at least 8 apart for a later mode (tiles of 64 rows of
+// the flattened (l, r) index), or at least 64 columns for the first mode.
+// Returns false when some mode does not qualify.
 bool make_oz_passes(const sylv_plan_s &p, std::vector<sylv_plan_s::OzPass> &out) {
     out.clear();
     if (p.Nm == 0) return false;
     const int64_t tot = p.ntot * p.nrhs;
     for (int j = 0; j < p.Nm; ++j) {
         const int64_t n = p.n[j], L = p.S[j];
-        if (n < 8 || n > 64 || n % 8) return false;
+        if (n < 8 || n > 64) return false;
         sylv_plan_s::OzPass o;
         o.j = j;
         o.n = (int)n;
@@ -240,10 +244,10 @@ bool make_oz_passes(const sylv_plan_s &p, std::vector<sylv_plan_s::OzPass> &out)
         o.R = tot / (L * n);
         if (o.mode1) {
             if (o.R < 64) return false;
-        } else if (L < 64) {
+        } else if (L < 8 || L >= ((int64_t)1 << 30)) {
             return false;
         }
-        o.tilesL = o.mode1 ? 1 : (L + 63) / 64;
+        o.tilesL = 1;
         o.Kp = (int)((n + 15) / 16 * 16);
         o.Np = (int)((2 * n + 15) / 16 * 16);
         if (o.mode1) {              // lanes along k: K-adjacent core matrices one padded column apart
@@ -613,7 +617,7 @@ cudaError_t run_groups(Ctx &c, const std::vector<Group> &gs, bool fp64, int whic
             t.L = g.L; t.R = g.R; t.tilesL = g.tilesL;
             t.flags = c.flags;
             t.done = done;
-            const int64_t tiles = g.mode1 ? (g.R + 63) / 64 : g.tilesL * g.R;
+            const int64_t tiles = g.mode1 ? (g.R + 63) / 64 : (g.L * g.R + 63) / 64;
             const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, p->num_sms));
             cudaError_t e = launch_modeprod_tc(epi, t, grid, g.smem, c.st);
             if (e != cudaSuccess) return e;
@@ -681,7 +685,7 @@ cudaError_t run_residual_oz(Ctx &c, const void *B, const void *X, void *Rdf, voi
         a.L = o.L; a.R = o.R; a.tilesL = o.tilesL;
         a.flags = c.flags;
         a.done = done;
-        const int64_t tiles = o.mode1 ? (o.R + 63) / 64 : o.tilesL * o.R;
+        const int64_t tiles = o.mode1 ? (o.R + 63) / 64 : (o.L * o.R + 63) / 64;
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, p->num_sms));
         cudaError_t e = launch_resid_oz(a, k == 0, k + 1 == np, grid, o.smem, c.st);
         if (e != cudaSuccess) return e;

@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_modeprod_tc(const __grid_cons
     const uint32_t bhi = smem_u32(Bhi), blo = smem_u32(Blo);
     const int64_t L = a.L;
     const bool evenL = (L & 1) == 0;
-    const int64_t ntile = M1 ? (a.R + 63) / 64 : a.tilesL * a.R;
+    const int64_t ntile = M1 ? (a.R + 63) / 64 : (L * a.R + 63) / 64;
     const int half_n = n >> 1;
     uint32_t phase[2] = {0u, 0u};
     float nd = 0.f, nx = 0.f;
@@ -139,32 +139,36 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_modeprod_tc(const __grid_cons
             }
             return;
         }
-        const int64_t rr = t / a.tilesL;
-        const int64_t ll0 = (t % a.tilesL) * 64;
-        const int lvv = (int)((L - ll0) < 64 ? (L - ll0) : 64);
-        const float *src = reinterpret_cast<const float *>(a.in) + 2 * (ll0 + rr * L * n);
+        // rows P = 64 t + d (d < 64) of the flattened (l, r) index, l = P mod L
+        const int64_t P0 = t * 64;
+        const int64_t r0 = P0 / L;
+        const int l0 = (int)(P0 - r0 * L);
+        const int64_t LR = L * a.R;
+        const float *in = reinterpret_cast<const float *>(a.in);
 #pragma unroll
         for (int b = 0; b < TC_NU; ++b) {
             const int u = warp + TC_WARPS * b;
             const int m4 = (u & 3) * 8 + (lane & 7);
             const int k = (u >> 2) * 4 + (lane >> 3);
             x[b][0] = x[b][1] = x[b][2] = x[b][3] = 0.f;
-            if (u < Kp && k < n) {
-                // 16-byte loads need an even L (the k stride is 8 L bytes); else 8-byte
-                const float *p = src + 2 * (int64_t)k * L + 4 * m4;
-                if (2 * m4 + 1 < lvv) {
-                    if (evenL) {
-                        const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
-                        x[b][0] = v.x; x[b][1] = v.y; x[b][2] = v.z; x[b][3] = v.w;
-                    } else {
-                        const float2 v0 = __ldg(reinterpret_cast<const float2 *>(p));
-                        const float2 v1 = __ldg(reinterpret_cast<const float2 *>(p + 2));
-                        x[b][0] = v0.x; x[b][1] = v0.y; x[b][2] = v1.x; x[b][3] = v1.y;
-                    }
-                } else if (2 * m4 < lvv) {
+            if (u < Kp && k < n && P0 + 2 * m4 < LR) {
+                const int q = (l0 + 2 * m4) / (int)L;
+                const int l = l0 + 2 * m4 - q * (int)L;
+                const int64_t c0 = l + L * ((int64_t)k + (int64_t)n * (r0 + q));
+                const float *p = in + 2 * c0;
+                const bool second = P0 + 2 * m4 + 1 < LR;
+                if (second && l + 1 < L && evenL) {       // both rows adjacent: 16 bytes
+                    const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+                    x[b][0] = v.x; x[b][1] = v.y; x[b][2] = v.z; x[b][3] = v.w;
+                } else {
                     const float2 v0 = __ldg(reinterpret_cast<const float2 *>(p));
-                    x[b][0] = v0.x;
-                    x[b][1] = v0.y;
+                    x[b][0] = v0.x; x[b][1] = v0.y;
+                    if (second) {
+                        const int64_t c1 = l + 1 < L ? c0 + 1
+                                                     : L * ((int64_t)k + (int64_t)n * (r0 + q + 1));
+                        const float2 v1 = __ldg(reinterpret_cast<const float2 *>(in + 2 * c1));
+                        x[b][2] = v1.x; x[b][3] = v1.y;
+                    }
                 }
             }
         }
@@ -271,12 +275,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_modeprod_tc(const __grid_cons
             return;
         }
         // complex out[l, i]: lane c of a pair stores the columns i0 + 2t + c
-        // (t < 8) after one exchange per column pair
-        const int64_t r = t / a.tilesL;
-        const int64_t l0 = (t % a.tilesL) * 64;
-        const int lv = (int)((L - l0) < 64 ? (L - l0) : 64);
-        const bool live = ll < lv;
-        const int64_t base = l0 + ll + r * L * n;            // complex index of (l, 0)
+        // (t < 8) after one exchange per column pair; row pair ll is the
+        // flattened row P = 64 t + ll
+        const int64_t P = t * 64 + ll;
+        const bool live = P < L * a.R;
+        const int64_t rP = P / L;
+        const int64_t base = (P - rP * L) + L * n * rP;          // complex index of (l, 0, r)
         for (int i0 = 16 * quarter; i0 < n; i0 += 64) {
             uint32_t va[16], vb[16];
             tmem_ld16(trow + (uint32_t)i0, va);

@@ -25,9 +25,9 @@
 // issues FP64 arithmetic; the last pass rounds R to complex64, the input of the
 // correction solve.
 //
-// Tiles follow the tensor-core transform pass: 64 consecutive l of one r for a
-// mode with L >= 64 (M1 = 0), 64 consecutive columns for the first mode
-// (M1 = 1).  The GEMM per digit pair is D(128 x 2n) = Xd(128 x n) Ad(n x 2n),
+// Tiles follow the tensor-core transform pass: 64 consecutive rows of the
+// flattened (l, r) index for a later mode (M1 = 0), 64 consecutive columns for
+// the first mode (M1 = 1).  The GEMM per digit pair is D(128 x 2n) = Xd(128 x n) Ad(n x 2n),
 // rows (p, re/im), columns [Re A^T | Im A^T].
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_resid_oz(const __grid_constan
     const int escale = eX + a.eA - 16;                         // value = 2^escale * Horner sum
     const uint32_t idesc = idesc_bf16(128, Np);
     const int64_t L = a.L;
-    const int64_t ntile = M1 ? (a.R + 63) / 64 : a.tilesL * a.R;
+    const int64_t ntile = M1 ? (a.R + 63) / 64 : (L * a.R + 63) / 64;
     const int ksteps = Kp / 16;
     uint32_t phase = 0;
 
@@ -184,9 +184,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_resid_oz(const __grid_constan
             p0 = t * 64;
             pv = (int)((a.R - p0) < 64 ? (a.R - p0) : 64);
         } else {
-            r = t / a.tilesL;
-            p0 = (t % a.tilesL) * 64;
-            pv = (int)((L - p0) < 64 ? (L - p0) : 64);
+            // rows P = 64 t + p of the flattened (l, r) index: r = first row's r,
+            // p0 = first row's l
+            const int64_t P0 = t * 64, LR = L * a.R;
+            r = P0 / L;
+            p0 = P0 - r * L;
+            pv = (int)((LR - P0) < 64 ? (LR - P0) : 64);
         }
     };
     auto coord = [&](int e, int &p, int &k) {
@@ -194,7 +197,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_resid_oz(const __grid_constan
         else { p = e & 63; k = e >> 6; }
     };
     auto gidx = [&](int64_t r, int64_t p0, int p, int k) -> int64_t {
-        return M1 ? (p0 + p) * n + k : (p0 + p) + L * ((int64_t)k + (int64_t)n * r);
+        if (M1) return (p0 + p) * n + k;
+        const int q = (int)(p0 + p) / (int)L;                 // rows past the end of r
+        const int64_t l = p0 + p - (int64_t)q * L;
+        return l + L * ((int64_t)k + (int64_t)n * (r + q));
     };
     auto fetch = [&](int64_t t) {
         int64_t r, p0;
@@ -377,7 +383,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_resid_oz(const __grid_constan
 
 cudaError_t launch_resid_oz(const OzArgs &a, int first, int last, int grid, size_t smem,
                             cudaStream_t st) {
-    if (a.n < 8 || a.n > 64 || (a.n & 7)) return cudaErrorInvalidValue;
+    if (a.n < 8 || a.n > 64) return cudaErrorInvalidValue;
 #define SYLV_OZ_LAUNCH(m1, f, l) k_resid_oz<m1, f, l><<<grid, OZ_THREADS, smem, st>>>(a)
     if (a.mode1) {
         if (first && last) SYLV_OZ_LAUNCH(1, 1, 1);

@@ -34,8 +34,11 @@ def _solve(A, B, **kw):
     ((64,), 64, True),                # one mode: the first pass is also the last
     ((64, 24, 1, 8), 1, True),
     ((16, 8, 24, 2), 3, False),       # n = 2: the residual stays FP64
-    ((48, 16, 8), 2, False),          # second mode with only 48 rows before it
-    ((70, 5), 1, False),
+    ((48, 16, 8), 2, True),           # later modes with 48 and 768 rows before them
+    ((40, 12, 20), 2, True),          # sizes that are not multiples of 8 (K padded)
+    ((64, 24, 9), 1, True),
+    ((70, 5), 1, False),              # n = 70 > 64
+    ((4, 16, 16), 1, False),          # n = 4 < 8
 ])
 def test_emu_matches_oracle(shape, nrhs, on_tc):
     p = si.random_problem(shape, nrhs, seed=sum(shape) + 3 * nrhs)

@@ -69,6 +69,9 @@ SHAPES = [
     ((600, 9), 1), ((130, 3, 2), 2),
     # first mode on the tensor cores (n % 8 == 0, 32 <= n <= 80, >= 64 columns)
     ((64, 70), 1), ((48, 5, 16), 2), ((80, 9, 8), 1), ((32, 32, 32), 1), ((40, 2, 33), 2),
+    # later modes on the tensor cores with fewer than 64 rows before them (tiles of
+    # the flattened (l, r) index; odd L takes the 8-byte loads)
+    ((48, 40, 3), 2), ((9, 33, 2), 3), ((12, 5, 48), 1),
 ]
 
 
@@ -136,7 +139,8 @@ def test_errors_are_reported():
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("shape", [(8, 8, 8), (13, 1, 9, 4), (2, 2, 3, 2, 2), (64, 70),
-                                   (48, 5, 16), (40, 2, 33), (80, 9, 8)])
+                                   (48, 5, 16), (40, 2, 33), (80, 9, 8), (48, 40, 3),
+                                   (9, 33, 2)])
 def test_phases_with_the_plans_factors(shape, prec):
     p = si.random_problem(shape, 2, seed=len(shape))
     plan = Plan(A=p.A, nrhs=2, prec=prec)
