@@ -422,13 +422,19 @@ sylv_status build_sweep(const sylv_plan_s &p, const int *b, int threads, SweepCo
         for (int e = 0; e < a.Pt; ++e) sched[pos[lvl[e]]++] = e;
     }
     // for full tiles: the schedule as box offsets, and every box offset's
-    // in-tile coordinates packed 8 bits per mode
+    // in-tile coordinates packed into 64 bits, ceil(log2 b) bits per mode
     a.bmax = 1;
-    a.fast = a.nin <= 8 ? 1 : 0;
+    int cbits = 0;
     for (int q = 0; q < a.nin; ++q) {
-        a.bmax = std::max(a.bmax, a.b[a.inmode[q]]);
-        if (a.b[a.inmode[q]] > 255) a.fast = 0;
+        const int bq = a.b[a.inmode[q]];
+        a.bmax = std::max(a.bmax, bq);
+        int w = 1;
+        while ((1 << w) < bq) ++w;
+        a.cshift[q] = cbits;
+        a.cmask[q] = (1u << w) - 1u;
+        cbits += w;
     }
+    a.fast = cbits <= 64 ? 1 : 0;
     std::vector<int> sched_e(a.Pt, 0);
     std::vector<unsigned long long> coord(a.Pt, 0ull);
     for (int qq = 0; qq < a.Pt; ++qq) {
@@ -444,7 +450,7 @@ sylv_status build_sweep(const sylv_plan_s &p, const int *b, int threads, SweepCo
         for (int e = 0; e < a.Pt; ++e) {
             unsigned long long c = 0;
             for (int q = 0; q < a.nin; ++q)
-                c |= (unsigned long long)((e / a.BS[q]) % a.b[a.inmode[q]]) << (8 * q);
+                c |= (unsigned long long)((e / a.BS[q]) % a.b[a.inmode[q]]) << a.cshift[q];
             coord[e] = c;
         }
 

@@ -219,6 +219,145 @@ __global__ void __launch_bounds__(256) k_modeprod(const __grid_constant__ MPArgs
     }
 }
 
+// FP32 pass over a group of G adjacent modes that all have n = 2 (the small-n
+// workloads): the 2 x 2 products are radix-2 butterflies between tile entries
+// whose p indices differ in one bit.  Instead of G shared-memory sweeps, the
+// tile is staged once; butterflies on the five lowest bits of p run across the
+// lanes of a warp (shuffles) when the tile's rows are single entries (Lt = 1),
+// and the other bits run in registers, four bits per round, each thread
+// holding the 16 entries of one base index (consecutive threads on consecutive
+// shared-memory words).  The epilogue is the general pass's.
+template <typename Tin, typename Tout, int EPI>
+__global__ void __launch_bounds__(256) k_modeprod_n2(const __grid_constant__ MPArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ float2 Ms[MAXG][4];                 // 2 x 2 matrices, column-major
+    if (a.done && *(volatile const int *)a.done) return;
+
+    const int Lt = a.Lt, Rt = a.Rt, G = a.G;
+    const int P = 1 << G;
+    const int E = Lt * P * Rt;
+    float2 *buf = reinterpret_cast<float2 *>(smem_raw);
+    const int64_t tl = (int64_t)blockIdx.x % a.tilesL;
+    const int64_t tr = (int64_t)blockIdx.x / a.tilesL;
+    const int64_t l0 = tl * Lt, r0 = tr * Rt;
+    const int64_t L = a.L, R = a.R;
+    const int lv = (int)((L - l0) < Lt ? (L - l0) : Lt);
+    const int rv = (int)((R - r0) < Rt ? (R - r0) : Rt);
+    const Tin *in = reinterpret_cast<const Tin *>(a.in);
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+
+    if (tid < 4 * G)
+        Ms[tid >> 2][tid & 3] = __ldg(reinterpret_cast<const float2 *>(a.mats[tid >> 2]) + (tid & 3));
+    for (int t = tid; t < E; t += nt) {
+        const int l = t % Lt;
+        const int rest = t / Lt;
+        const int p = rest & (P - 1);
+        const int r = rest >> G;
+        float2 v = make_float2(0.f, 0.f);
+        if (l < lv && r < rv) v = to_c(in[(l0 + l) + L * ((int64_t)p + a.P * (r0 + r))], float());
+        buf[t] = v;
+    }
+    __syncthreads();
+
+    // y_i = M[i, 0] x_0 + M[i, 1] x_1 for the pair (x_0, x_1) along mode m
+    auto bfly = [&](int m, float2 &x0, float2 &x1) {
+        const float2 m00 = Ms[m][0], m10 = Ms[m][1], m01 = Ms[m][2], m11 = Ms[m][3];
+        float2 y0 = make_float2(0.f, 0.f), y1 = make_float2(0.f, 0.f);
+        cmac(y0, m00, x0); cmac(y0, m01, x1);
+        cmac(y1, m10, x0); cmac(y1, m11, x1);
+        x0 = y0;
+        x1 = y1;
+    };
+    int m0 = 0;
+    if (Lt == 1) {
+        // bits 0..w-1 of p across the lanes: 32 consecutive entries per warp step
+        const int w = G < 5 ? G : 5;
+        for (int base = (tid & ~31); base < E; base += nt) {
+            const int t = base + lane;
+            float2 x = t < E ? buf[t] : make_float2(0.f, 0.f);
+            for (int b = 0; b < w; ++b) {
+                const float2 y = make_float2(__shfl_xor_sync(0xffffffffu, x.x, 1 << b),
+                                             __shfl_xor_sync(0xffffffffu, x.y, 1 << b));
+                const bool hi = (lane >> b) & 1;
+                const float2 mx = Ms[b][hi ? 3 : 0], my = Ms[b][hi ? 1 : 2];  // M[hi,hi], M[hi,1-hi]
+                float2 o = make_float2(0.f, 0.f);
+                cmac(o, mx, x);
+                cmac(o, my, y);
+                x = o;
+            }
+            if (t < E) buf[t] = x;
+        }
+        m0 = w;
+        __syncthreads();
+    }
+    // remaining bits in registers, up to four per round
+    for (; m0 < G; m0 += 4) {
+        const int k = (G - m0) < 4 ? (G - m0) : 4;
+        const int nb = E >> k;
+        const int hib = G - m0 - k;                 // bits of p above the round
+        for (int bi = tid; bi < nb; bi += nt) {
+            const int l = bi % Lt;
+            int rest = bi / Lt;
+            const int plo = rest & ((1 << m0) - 1);
+            rest >>= m0;
+            const int phi = rest & ((1 << hib) - 1);
+            const int r = rest >> hib;
+            const int tb = l + Lt * (plo + (phi << (m0 + k)) + P * r);
+            const int st = Lt << m0;
+            float2 x[16];
+#pragma unroll
+            for (int s2 = 0; s2 < 16; ++s2)
+                if (s2 < (1 << k)) x[s2] = buf[tb + st * s2];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                if (b >= k) break;
+#pragma unroll
+                for (int s2 = 0; s2 < 16; ++s2)
+                    if (s2 < (1 << k) && !((s2 >> b) & 1)) bfly(m0 + b, x[s2], x[s2 | (1 << b)]);
+            }
+#pragma unroll
+            for (int s2 = 0; s2 < 16; ++s2)
+                if (s2 < (1 << k)) buf[tb + st * s2] = x[s2];
+        }
+        __syncthreads();
+    }
+
+    float nd = 0.f, nx = 0.f;
+    for (int t = tid; t < E; t += nt) {
+        const int l = t % Lt;
+        const int rest = t / Lt;
+        const int p = rest & (P - 1);
+        const int r = rest >> G;
+        if (l >= lv || r >= rv) continue;
+        const int64_t g = (l0 + l) + L * ((int64_t)p + a.P * (r0 + r));
+        const float2 acc = buf[t];
+        if (EPI == EPI_STORE) {
+            reinterpret_cast<Tout *>(a.out)[g] = to_c(acc, (decltype(Tout().x))0);
+        } else if (EPI == EPI_STORE_NORM) {
+            const double2 o = to_c(acc, double());
+            reinterpret_cast<double2 *>(a.out)[g] = o;
+            nx = fmaxf(nx, cabsmax(o));
+        } else if (EPI == EPI_ACCUM) {
+            double2 *Xp = reinterpret_cast<double2 *>(a.out);
+            double2 x = Xp[g];
+            const double2 dd = to_c(acc, double());
+            x.x += dd.x;
+            x.y += dd.y;
+            Xp[g] = x;
+            nd = fmaxf(nd, cabsmax(dd));
+            nx = fmaxf(nx, cabsmax(x));
+        }
+    }
+    if (EPI == EPI_STORE_NORM || EPI == EPI_ACCUM) {
+        nd = warp_max(nd);
+        nx = warp_max(nx);
+        if (lane == 0) {
+            if (EPI == EPI_ACCUM) atomic_max_nonneg(&a.flags->dmax, nd);
+            atomic_max_nonneg(&a.flags->xmax, nx);
+        }
+    }
+}
+
 template <typename real, typename Tin, typename Tout, int EPI>
 static cudaError_t set_smem_attr() {
     return cudaFuncSetAttribute(k_modeprod<real, Tin, Tout, EPI>,
@@ -242,6 +381,21 @@ cudaError_t launch_modeprod(int fp64, int in_kind, int out_kind, int epi, const 
         else
             return cudaErrorInvalidValue;
     } else {
+        bool all2 = a.G >= 2 && a.Lt * ((int64_t)1 << a.G) * a.Rt <= (1 << 30);
+        for (int m = 0; m < a.G; ++m) all2 = all2 && a.gn[m] == 2;
+        if (all2) {                  // groups of n = 2 modes: butterflies
+            if (epi == EPI_STORE && in_kind == ELEM_C128 && out_kind == ELEM_C64)
+                k_modeprod_n2<double2, float2, EPI_STORE><<<grid, block, smem, st>>>(a);
+            else if (epi == EPI_STORE && in_kind == ELEM_C64 && out_kind == ELEM_C64)
+                k_modeprod_n2<float2, float2, EPI_STORE><<<grid, block, smem, st>>>(a);
+            else if (epi == EPI_STORE_NORM && in_kind == ELEM_C64 && out_kind == ELEM_C128)
+                k_modeprod_n2<float2, double2, EPI_STORE_NORM><<<grid, block, smem, st>>>(a);
+            else if (epi == EPI_ACCUM && in_kind == ELEM_C64 && out_kind == ELEM_C128)
+                k_modeprod_n2<float2, double2, EPI_ACCUM><<<grid, block, smem, st>>>(a);
+            else
+                return cudaErrorInvalidValue;
+            return cudaGetLastError();
+        }
         if (epi == EPI_STORE && in_kind == ELEM_C128 && out_kind == ELEM_C64)
             k_modeprod<float, double2, float2, EPI_STORE><<<grid, block, smem, st>>>(a);
         else if (epi == EPI_STORE && in_kind == ELEM_C64 && out_kind == ELEM_C64)
@@ -376,6 +530,16 @@ cudaError_t kernels_init(int) {
     if ((e = set_smem_attr<float, float2, float2, EPI_STORE>()) != cudaSuccess) return e;
     if ((e = set_smem_attr<float, float2, double2, EPI_STORE_NORM>()) != cudaSuccess) return e;
     if ((e = set_smem_attr<float, float2, double2, EPI_ACCUM>()) != cudaSuccess) return e;
+    const int big = 200 * 1024;
+    if ((e = cudaFuncSetAttribute(k_modeprod_n2<double2, float2, EPI_STORE>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_modeprod_n2<float2, float2, EPI_STORE>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_modeprod_n2<float2, double2, EPI_STORE_NORM>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_modeprod_n2<float2, double2, EPI_ACCUM>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess)
+        return e;
     if ((e = modeprod_tc_init_attrs()) != cudaSuccess) return e;
     if ((e = resid_oz_init_attrs()) != cudaSuccess) return e;
     return sweep_init_attrs();

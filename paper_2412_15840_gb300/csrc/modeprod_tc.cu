@@ -103,6 +103,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_modeprod_tc(const __grid_cons
     const uint32_t bhi = smem_u32(Bhi), blo = smem_u32(Blo);
     const int64_t L = a.L;
     const bool evenL = (L & 1) == 0;
+    const bool aligned = (L & 63) == 0;
     const int64_t ntile = M1 ? (a.R + 63) / 64 : (L * a.R + 63) / 64;
     const int half_n = n >> 1;
     uint32_t phase[2] = {0u, 0u};
@@ -152,7 +153,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_modeprod_tc(const __grid_cons
             const int k = (u >> 2) * 4 + (lane >> 3);
             x[b][0] = x[b][1] = x[b][2] = x[b][3] = 0.f;
             if (u < Kp && k < n && P0 + 2 * m4 < LR) {
-                const int q = (l0 + 2 * m4) / (int)L;
+                // (a tile never straddles two r when 64 divides L)
+                const int q = aligned ? 0 : (l0 + 2 * m4) / (int)L;
                 const int l = l0 + 2 * m4 - q * (int)L;
                 const int64_t c0 = l + L * ((int64_t)k + (int64_t)n * (r0 + q));
                 const float *p = in + 2 * c0;
@@ -279,7 +281,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_modeprod_tc(const __grid_cons
         // flattened row P = 64 t + ll
         const int64_t P = t * 64 + ll;
         const bool live = P < L * a.R;
-        const int64_t rP = P / L;
+        const int64_t rP = aligned ? (t * 64) / L : P / L;
         const int64_t base = (P - rP * L) + L * n * rP;          // complex index of (l, 0, r)
         for (int i0 = 16 * quarter; i0 < n; i0 += 64) {
             uint32_t va[16], vb[16];

@@ -171,6 +171,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_resid_oz(const __grid_constan
     const int escale = eX + a.eA - 16;                         // value = 2^escale * Horner sum
     const uint32_t idesc = idesc_bf16(128, Np);
     const int64_t L = a.L;
+    const bool aligned = (L & 63) == 0;      // 64-row tiles never straddle two r
     const int64_t ntile = M1 ? (a.R + 63) / 64 : (L * a.R + 63) / 64;
     const int ksteps = Kp / 16;
     uint32_t phase = 0;
@@ -198,7 +199,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_resid_oz(const __grid_constan
     };
     auto gidx = [&](int64_t r, int64_t p0, int p, int k) -> int64_t {
         if (M1) return (p0 + p) * n + k;
-        const int q = (int)(p0 + p) / (int)L;                 // rows past the end of r
+        const int q = aligned ? 0 : (int)(p0 + p) / (int)L;   // rows past the end of r
         const int64_t l = p0 + p - (int64_t)q * L;
         return l + L * ((int64_t)k + (int64_t)n * (r + q));
     };

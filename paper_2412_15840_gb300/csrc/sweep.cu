@@ -14,11 +14,13 @@
 //
 // One tile, three stages:
 //  1. load C, form the FP64 reciprocal of sigma + sum_j t_{j,i_j i_j} for
-//     every entry, then subtract the contributions of the solved tiles mode
-//     by mode as a small GEMM: T_j[rows of the block, later columns] times the
-//     strip of solved values.  One thread owns a fiber of the tile along mode
-//     j, loads every strip value once and applies all b_j rows of the T block
-//     (staged in shared memory) to it.
+//     every entry (or read it from the plan's table) and subtract, entry by
+//     entry, the strips of the modes outside the tile; then subtract the
+//     contributions of the solved tiles along the in-tile modes, mode by mode,
+//     as a small GEMM: T_j[rows of the block, later columns] times the strip of
+//     solved values.  A fiber of the tile along mode j belongs to one thread
+//     (or a few adjacent lanes), which loads every strip value once and applies
+//     all b_j rows of the T block (staged in shared memory) to it.
 //  2. solve the tile in place, level by level of the in-tile index sum
 //     measured from the tile's end: the in-tile part of Eq. (yi1i2iN), then
 //     y = num * (1/den) with the reciprocal formed in FP64 in stage 1.
@@ -35,6 +37,7 @@ namespace sylv {
 
 constexpr int SW_KCH = SWEEP_KCH;
 constexpr int SW_RG = 8;     // fiber rows kept in registers at once
+constexpr int SW_OUT = 128;  // strip entries of the modes outside the tile applied in stage 1a
 // lanes sharing one entry in the in-tile wavefront: 4 on the FP32 path with
 // packed coordinates (its wavefront is latency-bound), else 1 (the FP64 path is
 // bound by the FP64 pipe; tiles of many small modes gain nothing)
@@ -82,6 +85,11 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
     __shared__ int64_t s_o[MAXM];
     __shared__ int s_be[MAXM], s_cnt[MAXM], s_I[MAXM];
     __shared__ int64_t s_gbase, s_rhs0;
+    // modes outside the tile (b_j = 1): the (offset, T value) pairs of their
+    // strips, applied entry by entry in stage 1a without extra barriers
+    __shared__ int s_npair, s_inlist[MAXM], s_pbase[MAXM];
+    __shared__ int64_t s_pstride[SW_OUT];
+    __shared__ C2 s_pt[SW_OUT];
     __shared__ double s_den0x, s_den0y;
 
     if (*(volatile const int *)&a.flags->done) return;
@@ -162,10 +170,34 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
             s_den0x = dx;
             s_den0y = dy;
             s_full = full && a.fast;
+            int np = 0;
+            for (int j = 0; j < Nm; ++j) {
+                s_inlist[j] = 0;
+                const int K = s_cnt[j];
+                if (a.qpos[j] >= 0 || K == 0 || np + K > SW_OUT) continue;
+                s_inlist[j] = 1;
+                s_pbase[j] = np;
+                np += K;
+            }
+            s_npair = np;
         }
         __syncthreads();
         const int64_t gbase = s_gbase;
         const bool full = s_full != 0;
+        const int npair = s_npair;
+        if (npair > 0) {
+            for (int j = 0; j < Nm; ++j) {
+                if (!s_inlist[j]) continue;
+                const int K = s_cnt[j], base = s_pbase[j];
+                const int64_t nj = a.n[j], oj = s_o[j];
+                const C2 *Tj = reinterpret_cast<const C2 *>(a.T[j]);
+                for (int k = threadIdx.x; k < K; k += nt) {
+                    s_pstride[base + k] = (int64_t)(1 + k) * a.S[j];
+                    s_pt[base + k] = __ldg(Tj + oj + (oj + 1 + k) * nj);
+                }
+            }
+            __syncthreads();
+        }
 
         // stage 1a: C and the FP64 reciprocals of the diagonal sums
         for (int e = threadIdx.x; e < a.Pt; e += nt) {
@@ -176,7 +208,7 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
                 const unsigned long long c = coord_s[e];
                 for (int q = 0; q < nin; ++q) {
                     const int j = a.inmode[q];
-                    const int t = (int)((c >> (8 * q)) & 255u);
+                    const int t = (int)((c >> a.cshift[q]) & a.cmask[q]);
                     g += (int64_t)t * a.S[j];
                     if (!a.inv_tab) {
                         const int64_t ij = s_o[j] + t;
@@ -202,7 +234,17 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
                 tile_s[e] = czero<C2>();
                 continue;
             }
-            tile_s[e] = __ldcg(Y + g);
+            C2 cv = __ldcg(Y + g);
+            for (int p0 = 0; p0 < npair; p0 += 4) {        // 4 strip loads in flight
+                C2 y[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (p0 + u < npair) y[u] = __ldcg(Y + g + s_pstride[p0 + u]);
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (p0 + u < npair) cmsub(cv, s_pt[p0 + u], y[u]);
+            }
+            tile_s[e] = cv;
             if (a.inv_tab)       // reciprocals formed once per plan (k_inv_table)
                 inv_s[e] = __ldg(reinterpret_cast<const Inv *>(a.inv_tab) + (g - s_rhs0));
             else
@@ -225,7 +267,7 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
         // stage 1b: contributions of the solved tiles, mode by mode
         for (int j = 0; j < Nm; ++j) {
             const int K = s_cnt[j];
-            if (K == 0) continue;
+            if (K == 0 || s_inlist[j]) continue;
             const int q = a.qpos[j];
             const int bj = q >= 0 ? a.b[j] : 1;     // box extent along mode j
             const int bej = s_be[j];                // valid rows of the block
@@ -257,7 +299,7 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
                     if (ok && full) {
                         const unsigned long long c = coord_s[e0];
                         for (int p = 0; p < nin; ++p)
-                            g0 += (int64_t)((c >> (8 * p)) & 255u) * a.S[a.inmode[p]];
+                            g0 += (int64_t)((c >> a.cshift[p]) & a.cmask[p]) * a.S[a.inmode[p]];
                     } else if (ok) {
                         int r = e0;
                         for (int p = 0; p < nin; ++p) {
@@ -376,7 +418,7 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
                     for (int p = sub; p < nin; p += SW_SUB) {
                         const int j = a.inmode[p];
                         const int bs = a.BS[p];
-                        const int t = full ? (int)((c >> (8 * p)) & 255u) : (e / bs) % a.b[j];
+                        const int t = full ? (int)((c >> a.cshift[p]) & a.cmask[p]) : (e / bs) % a.b[j];
                         const int be = s_be[j];
                         if (t + 1 >= be) continue;
                         const int bj = a.b[j];
@@ -410,7 +452,7 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
             if (full) {
                 const unsigned long long c = coord_s[e];
                 for (int p = 0; p < nin; ++p)
-                    g += (int64_t)((c >> (8 * p)) & 255u) * a.S[a.inmode[p]];
+                    g += (int64_t)((c >> a.cshift[p]) & a.cmask[p]) * a.S[a.inmode[p]];
             } else {
                 int r = e;
                 for (int p = 0; p < nin; ++p) {

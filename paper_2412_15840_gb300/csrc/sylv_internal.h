@@ -73,7 +73,9 @@ struct SweepArgs {
     int Lin;                  // in-tile levels
     int Pt;                   // entries of a full tile
     int bmax;                 // largest in-tile block extent
-    int fast;                 // packed coordinates available (<= 8 in-tile modes, b <= 255)
+    int fast;                 // packed coordinates available (their widths fit 64 bits)
+    int cshift[MAXM];         // bit offset of in-tile mode q in a packed coordinate
+    unsigned cmask[MAXM];     // its mask (ceil(log2 b) bits)
     double den_scale;         // power of two keeping |scale * diagonal sum|^2 in range
     int64_t n[MAXM];
     int64_t S[MAXM];          // element strides

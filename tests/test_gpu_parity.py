@@ -140,7 +140,7 @@ def test_errors_are_reported():
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("shape", [(8, 8, 8), (13, 1, 9, 4), (2, 2, 3, 2, 2), (64, 70),
                                    (48, 5, 16), (40, 2, 33), (80, 9, 8), (48, 40, 3),
-                                   (9, 33, 2)])
+                                   (9, 33, 2), (2,) * 7, (2,) * 14, (3, 2, 2, 2, 2, 2)])
 def test_phases_with_the_plans_factors(shape, prec):
     p = si.random_problem(shape, 2, seed=len(shape))
     plan = Plan(A=p.A, nrhs=2, prec=prec)
