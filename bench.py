@@ -232,7 +232,7 @@ def other_workload(args, local: int) -> int:
     Bs = [to_device(p.B, device=dev) for p in probs]
     out = {"workload": name, "description": desc, "entries": entries, "equations": len(probs)}
     stream = torch.cuda.current_stream(dev)
-    for prec in ("mixed", "fp64"):
+    for prec in ("mixed", "fp64", "mixed_emu"):
         t0 = time.perf_counter()
         plans = [Plan(A=p.A, nrhs=p.nrhs, prec=prec, rtol=RTOL, max_refine=MAX_REFINE,
                       device=local) for p in probs]
@@ -258,6 +258,9 @@ def other_workload(args, local: int) -> int:
         rec = {"ms_per_step": ms, "value": entries / (ms * 1e-3), "setup_s": setup,
                "max_refine_iters": max(i["refine_iters"] for i in infos),
                "status": sorted({i["status"] for i in infos})}
+        if prec == "mixed_emu":
+            rec["tensor_core_residual_equations"] = sum(
+                1 for i in infos if i["tensor_core_residual"])
         if name in ("batch512", "advdiff48"):
             pick = [min(range(len(probs)), key=lambda e: probs[e].n_tot)] if name == "batch512" \
                 else [0]

@@ -40,12 +40,12 @@ struct Group {
 // 8 positions apart (tiles of 64 rows of the flattened (l, r) index stay
 // mostly contiguous) and the operands fit in shared memory.
 bool tc_mode_ok(int64_t L, int64_t n) {
-    return L >= 8 && L < ((int64_t)1 << 30) && n >= 32 && n <= 80;
+    return L >= 8 && L < ((int64_t)1 << 30) && n >= 16 && n <= 80;
 }
 // The first mode (contiguous fibres) runs on the tensor cores with tiles of 64
 // columns when it is not the last pass of a transform and n is a multiple of 8.
 bool tc_mode1_ok(int64_t n, int64_t cols, int Nm) {
-    return Nm >= 2 && n % 8 == 0 && n >= 32 && n <= 80 && cols >= 64;
+    return Nm >= 2 && n % 8 == 0 && n >= 16 && n <= 80 && cols >= 64;
 }
 
 void tc_geometry(Group &g, int n, bool mode1) {

@@ -77,8 +77,8 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
     C2 *tile_s = reinterpret_cast<C2 *>(inv_s + a.Pt);
     C2 *Ts = tile_s + a.Pt;                       // SW_KCH x bmax block of T_j
     C2 *Td = Ts + SW_KCH * a.bmax;                // diagonal blocks of the in-tile modes
-    // full tiles: packed in-tile coordinates and the level schedule, copied
-    // once per CTA (every full tile uses the same tables)
+    // packed in-tile coordinates and the level schedule of the full box, copied
+    // once per CTA (every tile uses the same tables)
     unsigned long long *coord_s = reinterpret_cast<unsigned long long *>(Td + a.tdsize);
     int *sched_s = reinterpret_cast<int *>(coord_s + (a.fast ? a.Pt : 0));
     __shared__ int s_ticket, s_tile, s_abort, s_full;
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
             s_rhs0 = rhs * a.ntot;
             s_den0x = dx;
             s_den0y = dy;
-            s_full = full && a.fast;
+            s_full = full;
             int np = 0;
             for (int j = 0; j < Nm; ++j) {
                 s_inlist[j] = 0;
@@ -183,7 +183,9 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
         }
         __syncthreads();
         const int64_t gbase = s_gbase;
-        const bool full = s_full != 0;
+        // packed coordinates serve every tile; a partial tile (be_j < b_j for some
+        // in-tile mode) skips the box offsets outside its valid extents
+        const bool fastc = a.fast != 0, partial = s_full == 0;
         const int npair = s_npair;
         if (npair > 0) {
             for (int j = 0; j < Nm; ++j) {
@@ -204,11 +206,12 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
             int64_t g = gbase;
             bool ok = true;
             double ex = s_den0x, ey = s_den0y;
-            if (full) {
+            if (fastc) {
                 const unsigned long long c = coord_s[e];
                 for (int q = 0; q < nin; ++q) {
                     const int j = a.inmode[q];
                     const int t = (int)((c >> a.cshift[q]) & a.cmask[q]);
+                    if (partial && t >= s_be[j]) { ok = false; break; }
                     g += (int64_t)t * a.S[j];
                     if (!a.inv_tab) {
                         const int64_t ij = s_o[j] + t;
@@ -296,10 +299,13 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
                     const int e0 = (q >= 0) ? (f / bs) * (bs * bj) + (f % bs) : f;
                     int64_t g0 = gbase;
                     bool ok = f < F;
-                    if (ok && full) {
+                    if (ok && fastc) {
                         const unsigned long long c = coord_s[e0];
-                        for (int p = 0; p < nin; ++p)
-                            g0 += (int64_t)((c >> a.cshift[p]) & a.cmask[p]) * a.S[a.inmode[p]];
+                        for (int p = 0; p < nin; ++p) {
+                            const int t = (int)((c >> a.cshift[p]) & a.cmask[p]);
+                            if (partial && t >= s_be[a.inmode[p]]) { ok = false; break; }
+                            g0 += (int64_t)t * a.S[a.inmode[p]];
+                        }
                     } else if (ok) {
                         int r = e0;
                         for (int p = 0; p < nin; ++p) {
@@ -398,9 +404,13 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
                 int e = 0;
                 unsigned long long c = 0;
                 if (act) {
-                    if (full) {
+                    if (fastc) {
                         e = sched_s[qq];
                         c = coord_s[e];
+                        if (partial)
+                            for (int p = 0; p < nin; ++p)
+                                if ((int)((c >> a.cshift[p]) & a.cmask[p]) >= s_be[a.inmode[p]])
+                                    act = false;
                     } else {
                         int r = a.sched[qq];
                         for (int p = 0; p < nin; ++p) {
@@ -418,7 +428,8 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
                     for (int p = sub; p < nin; p += SW_SUB) {
                         const int j = a.inmode[p];
                         const int bs = a.BS[p];
-                        const int t = full ? (int)((c >> a.cshift[p]) & a.cmask[p]) : (e / bs) % a.b[j];
+                        const int t = fastc ? (int)((c >> a.cshift[p]) & a.cmask[p])
+                                            : (e / bs) % a.b[j];
                         const int be = s_be[j];
                         if (t + 1 >= be) continue;
                         const int bj = a.b[j];
@@ -449,10 +460,13 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
         for (int e = threadIdx.x; e < a.Pt; e += nt) {
             int64_t g = gbase;
             bool ok = true;
-            if (full) {
+            if (fastc) {
                 const unsigned long long c = coord_s[e];
-                for (int p = 0; p < nin; ++p)
-                    g += (int64_t)((c >> a.cshift[p]) & a.cmask[p]) * a.S[a.inmode[p]];
+                for (int p = 0; p < nin; ++p) {
+                    const int t = (int)((c >> a.cshift[p]) & a.cmask[p]);
+                    if (partial && t >= s_be[a.inmode[p]]) { ok = false; break; }
+                    g += (int64_t)t * a.S[a.inmode[p]];
+                }
             } else {
                 int r = e;
                 for (int p = 0; p < nin; ++p) {

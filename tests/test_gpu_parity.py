@@ -72,6 +72,8 @@ SHAPES = [
     # later modes on the tensor cores with fewer than 64 rows before them (tiles of
     # the flattened (l, r) index; odd L takes the 8-byte loads)
     ((48, 40, 3), 2), ((9, 33, 2), 3), ((12, 5, 48), 1),
+    # 16 <= n < 32 on the tensor cores (K padded to 8, N to 16)
+    ((19, 19, 19), 1), ((16, 17, 23), 2), ((24, 9, 21), 1),
 ]
 
 
@@ -140,7 +142,8 @@ def test_errors_are_reported():
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("shape", [(8, 8, 8), (13, 1, 9, 4), (2, 2, 3, 2, 2), (64, 70),
                                    (48, 5, 16), (40, 2, 33), (80, 9, 8), (48, 40, 3),
-                                   (9, 33, 2), (2,) * 7, (2,) * 14, (3, 2, 2, 2, 2, 2)])
+                                   (9, 33, 2), (2,) * 7, (2,) * 14, (3, 2, 2, 2, 2, 2),
+                                   (19, 19, 19), (16, 17, 23)])
 def test_phases_with_the_plans_factors(shape, prec):
     p = si.random_problem(shape, 2, seed=len(shape))
     plan = Plan(A=p.A, nrhs=2, prec=prec)
