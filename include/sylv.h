@@ -72,9 +72,15 @@ typedef enum {
                              sum_j ||A_j|| ||X|| instead of FP64 rounding.  Used when
                              every non-singleton mode has 8 <= n_j <= 64 and either
                              prod_{m<j} n_m >= 8 or (first mode) at least 64 columns
-                             (prod_{m>1} n_m times nrhs); otherwise the residual stays
-                             FP64 (sylv_info.path bit 1 tells which ran).  Entries of
-                             B and of the scaled products must lie in the FP32 range. */
+                             (prod_{m>1} n_m times nrhs), and when the ratio of the
+                             largest to the smallest |diagonal sum| (a lower bound of
+                             the condition number kappa) times 2^-44 is <= rtol: the
+                             refined error is about kappa 2^-45.  Otherwise the
+                             residual stays FP64 (sylv_info.path bit 1 tells which
+                             ran).  For strongly non-normal operators, whose kappa can
+                             far exceed that ratio, SYLV_MIXED_FP32 is the safe
+                             choice.  Entries of B and of the scaled products must lie
+                             in the FP32 range. */
 } sylv_prec;
 
 /* Per-solve report, filled (after a stream synchronisation) only when the

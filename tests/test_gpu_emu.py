@@ -94,3 +94,18 @@ def test_emu_evolve_and_batched():
     X0 = si.initial_state(q.shape, 2, seed=4)
     Xt = from_device(plans[0].evolve(0.2, Bs[0], to_device(X0)), q.B.shape)
     assert oracle.rel_err(Xt, oracle.evolve(q.A, q.B, X0, 0.2)) < 1e-10
+
+
+def test_emu_ill_conditioned_keeps_the_fp64_residual():
+    # eigenvalue sums spread over four decades: kappa 2^-45 would exceed rtol, so the
+    # plan keeps the FP64 residual and still reaches 1e-10
+    rng = np.random.default_rng(23)
+    A = []
+    for n in (64, 16, 8):
+        Q, _ = np.linalg.qr(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+        lam = np.geomspace(1e-4, 1.0, n) * np.exp(0.3j * rng.standard_normal(n))
+        A.append((Q * lam) @ Q.conj().T)
+    B = (rng.standard_normal((64, 16, 8, 1)) + 1j * rng.standard_normal((64, 16, 8, 1)))
+    X, info = _solve(A, B, max_refine=8)
+    assert info["status"] == 0 and not info["tensor_core_residual"]
+    assert oracle.rel_err(X, oracle.solve(A, B)) < 1e-10
