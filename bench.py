@@ -315,7 +315,7 @@ def evolve_workload(args, local: int) -> int:
            "entries": entries, "t": t}
     ref = None if args.no_oracle else oracle.evolve(p.A, p.B, X0, t)
     stream = torch.cuda.current_stream(dev)
-    for prec in ("mixed", "fp64"):
+    for prec in ("mixed", "fp64", "mixed_emu"):
         plan = Plan(A=p.A, nrhs=1, prec=prec, rtol=RTOL, max_refine=MAX_REFINE, device=local)
         X = torch.empty_like(Bd)
         ws = torch.empty(plan.evolve_workspace_bytes(), dtype=torch.uint8, device=dev)

@@ -149,8 +149,11 @@ struct sylv_plan_s {
         int ximg_bytes = 0, aimg_bytes = 0, tmem_cols = 0, eA = 0, rstage_off = 0;
         int64_t L = 1, R = 1, tilesL = 1;
         size_t smem = 0;
-        const unsigned char *aimg = nullptr;
+        const unsigned char *aimg = nullptr;   // digits of A_j (A_1 + sigma I)
+        const unsigned char *eimg = nullptr;   // digits of exp(t A_j) (sylv_evolve)
+        int eE = 0;                            // their scale exponent
     };
+    std::vector<unsigned char> Eimg_host;      // staging of the exp(t A_j) digits
     std::vector<OzPass> ozpasses;
     bool oz = false;              // every mode qualifies: the residual runs on the tensor cores
 
@@ -223,6 +226,37 @@ bool choose_tile(int64_t L, int64_t P, int64_t R, int64_t Et, int64_t Eh, int &L
     Lt = (int)lt;
     Rt = (int)rt;
     return true;
+}
+
+// [Re M^T | Im M^T] of an n x n complex matrix as 6 base-256 digits of |m| / 2^e
+// (bf16, the B-operand layout of the digit-product pass); returns e, with
+// |entries| < 2^(e - 1).
+template <typename Pass>
+int digit_images(const std::vector<std::complex<double>> &M, const Pass &o, unsigned char *img) {
+    const int n = o.n;
+    double amax = 0.0;
+    for (auto &z : M) amax = std::max(amax, std::max(std::fabs(z.real()), std::fabs(z.imag())));
+    const int e = amax > 0.0 ? std::ilogb(amax) + 2 : 0;
+    std::memset(img, 0, (size_t)6 * o.aimg_bytes);
+    for (int ii = 0; ii < 2 * n; ++ii)
+        for (int k = 0; k < n; ++k) {
+            const int i = ii < n ? ii : ii - n;
+            const std::complex<double> z = M[(size_t)(i + k * n)];
+            const double v = ii < n ? z.real() : z.imag();
+            const uint64_t F = (uint64_t)std::floor(std::ldexp(std::fabs(v), 48 - e));
+            const size_t off = (size_t)(ii / 8) * o.sboAd + (size_t)(k / 8) * 128 +
+                               (size_t)(ii % 8) * 16 + (size_t)(k % 8) * 2;
+            for (int u = 0; u < 6; ++u) {
+                const uint32_t d = (uint32_t)(F >> (40 - 8 * u)) & 0xFFu;
+                const float fd = (float)d;
+                uint32_t fb;
+                std::memcpy(&fb, &fd, 4);
+                uint16_t b = (uint16_t)(fb >> 16);        // exact: d has <= 8 bits
+                if (d && v < 0) b |= 0x8000u;
+                std::memcpy(img + (size_t)u * o.aimg_bytes + off, &b, 2);
+            }
+        }
+    return e;
 }
 
 // Residual passes on the tensor cores: every non-singleton mode needs
@@ -670,32 +704,50 @@ cudaError_t run_residual(Ctx &c, const void *B, const void *X, void *R, const in
 
 // R = B - sum_j A_j (x)_j X (sigma folded into the first mode) on the tensor
 // cores: FP32-pair R in `Rdf` between passes, complex64 R into `Rc64` at the end
+// one digit-product pass of mode pass k (tensor cores): out = base -/+ M (x)_j X
+cudaError_t run_oz_pass(Ctx &c, size_t k, const unsigned char *img, int eM, const void *X,
+                        const void *B, const void *Rin, void *Rout, void *Rc, int in_mode,
+                        int out_mode, int neg, float bsign, const int *done) {
+    sylv_plan_s *p = c.p;
+    const auto &o = p->ozpasses[k];
+    OzArgs a{};
+    a.X = X;
+    a.B = B;
+    a.Rin = Rin;
+    a.Rout = Rout;
+    a.Rc64 = Rc;
+    a.in_mode = in_mode;
+    a.out_mode = out_mode;
+    a.neg = neg;
+    a.bsign = bsign;
+    a.aimg = img;
+    a.n = o.n; a.Kp = o.Kp; a.Np = o.Np; a.mode1 = o.mode1;
+    a.lboX = o.lboX; a.sboX = o.sboX; a.sboAd = o.sboAd;
+    a.ximg_bytes = o.ximg_bytes; a.aimg_bytes = o.aimg_bytes;
+    a.rstage_off = o.rstage_off;
+    a.tmem_cols = o.tmem_cols; a.eA = eM;
+    a.L = o.L; a.R = o.R; a.tilesL = o.tilesL;
+    a.flags = c.flags;
+    a.done = done;
+    const int64_t tiles = o.mode1 ? (o.R + 63) / 64 : (o.L * o.R + 63) / 64;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, p->num_sms));
+    cudaError_t e = launch_resid_oz(a, grid, o.smem, c.st);
+    if (e == cudaSuccess) count(c);
+    return e;
+}
+
+// R = B - sum_j A_j (x)_j X (sigma folded into the first mode) on the tensor
+// cores: FP32-pair R in `Rdf` between passes, complex64 R into `Rc64` at the end
 cudaError_t run_residual_oz(Ctx &c, const void *B, const void *X, void *Rdf, void *Rc64,
                             const int *done) {
     sylv_plan_s *p = c.p;
     const size_t np = p->ozpasses.size();
     for (size_t k = 0; k < np; ++k) {
         const auto &o = p->ozpasses[k];
-        OzArgs a{};
-        a.X = X;
-        a.B = B;
-        a.Rin = Rdf;
-        a.Rout = Rdf;
-        a.Rc64 = Rc64;
-        a.aimg = o.aimg;
-        a.n = o.n; a.Kp = o.Kp; a.Np = o.Np; a.mode1 = o.mode1;
-        a.lboX = o.lboX; a.sboX = o.sboX; a.sboAd = o.sboAd;
-        a.ximg_bytes = o.ximg_bytes; a.aimg_bytes = o.aimg_bytes;
-        a.rstage_off = o.rstage_off;
-        a.tmem_cols = o.tmem_cols; a.eA = o.eA;
-        a.L = o.L; a.R = o.R; a.tilesL = o.tilesL;
-        a.flags = c.flags;
-        a.done = done;
-        const int64_t tiles = o.mode1 ? (o.R + 63) / 64 : (o.L * o.R + 63) / 64;
-        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, p->num_sms));
-        cudaError_t e = launch_resid_oz(a, k == 0, k + 1 == np, grid, o.smem, c.st);
+        cudaError_t e = run_oz_pass(c, k, o.aimg, o.eA, X, B, Rdf, Rdf, Rc64,
+                                    k == 0 ? OZ_IN_B : OZ_IN_PAIRS,
+                                    k + 1 == np ? OZ_OUT_C64 : OZ_OUT_PAIRS, 0, 1.f, done);
         if (e != cudaSuccess) return e;
-        count(c);
     }
     return cudaSuccess;
 }
@@ -1169,7 +1221,10 @@ sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t 
     reserve(3 * sizeof(unsigned long long));
     const size_t oz_first = offs.size();
     if (p->oz)
-        for (auto &o : p->ozpasses) reserve((size_t)6 * o.aimg_bytes);
+        for (auto &o : p->ozpasses) {
+            reserve((size_t)6 * o.aimg_bytes);     // A digits
+            reserve((size_t)6 * o.aimg_bytes);     // exp(t A) digits, filled by sylv_evolve
+        }
     const size_t diag_idx = offs.size();
     if (p->diag_sweep) reserve((size_t)diag_P1 * 16);
     const size_t tc_first = offs.size();
@@ -1280,30 +1335,11 @@ sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t 
             std::vector<cd> Am(p->Ah[p->orig[j]]);
             if (j == 0)
                 for (int i = 0; i < n; ++i) Am[(size_t)(i + i * n)] += p->sigma;
-            double amax = 0.0;
-            for (auto &z : Am) amax = std::max(amax, std::max(std::fabs(z.real()), std::fabs(z.imag())));
-            o.eA = amax > 0.0 ? std::ilogb(amax) + 2 : 0;
             unsigned char *img = reinterpret_cast<unsigned char *>(host.data()) + offs[oi2];
-            for (int ii = 0; ii < 2 * n; ++ii)
-                for (int k = 0; k < n; ++k) {
-                    const int i = ii < n ? ii : ii - n;
-                    const cd z = Am[(size_t)(i + k * n)];
-                    const double v = ii < n ? z.real() : z.imag();
-                    const uint64_t F = (uint64_t)std::floor(std::ldexp(std::fabs(v), 48 - o.eA));
-                    const size_t off = (size_t)(ii / 8) * o.sboAd + (size_t)(k / 8) * 128 +
-                                       (size_t)(ii % 8) * 16 + (size_t)(k % 8) * 2;
-                    for (int u = 0; u < 6; ++u) {
-                        const uint32_t d = (uint32_t)(F >> (40 - 8 * u)) & 0xFFu;
-                        const float fd = (float)d;
-                        uint32_t fb;
-                        std::memcpy(&fb, &fd, 4);
-                        uint16_t b = (uint16_t)(fb >> 16);        // exact: d has <= 8 bits
-                        if (d && v < 0) b |= 0x8000u;
-                        std::memcpy(img + (size_t)u * o.aimg_bytes + off, &b, 2);
-                    }
-                }
+            o.eA = digit_images(Am, o, img);
             o.aimg = (const unsigned char *)(base + offs[oi2]);
-            ++oi2;
+            o.eimg = (const unsigned char *)(base + offs[oi2 + 1]);
+            oi2 += 2;
         }
     }
     // diagonal-sweep head table: sigma + sum of t_{j,i_j i_j} over the head modes
@@ -1619,6 +1655,29 @@ sylv_status sylv_evolve(sylv_plan_t p, double t, const void *B, const void *X0, 
         p->evolve_eps = std::exp(t * p->sigma);
         if (!std::isfinite(p->evolve_eps.real()) || !std::isfinite(p->evolve_eps.imag()))
             return SYLV_ERR_INVALID_ARG;
+        if (p->oz) {
+            // digits of exp(t A_j) for the tensor-core passes (exp(t sigma) folded
+            // into the first mode)
+            size_t total = 0;
+            for (auto &o : p->ozpasses) total += (size_t)6 * o.aimg_bytes;
+            p->Eimg_host.assign(total, 0);
+            size_t off = 0;
+            for (auto &o : p->ozpasses) {
+                const int64_t nj = o.n;
+                std::vector<cd> Em((size_t)(nj * nj));
+                size_t base = 0;
+                for (int q = 0; q < o.j; ++q) base += (size_t)(2 * p->n[q] * p->n[q]);
+                for (size_t k = 0; k < Em.size(); ++k)
+                    Em[k] = cd(p->Ehost[base + 2 * k], p->Ehost[base + 2 * k + 1]) *
+                            (o.j == 0 ? p->evolve_eps : cd(1.0));
+                o.eE = digit_images(Em, o, p->Eimg_host.data() + off);
+                if (cudaMemcpyAsync(const_cast<unsigned char *>(o.eimg), p->Eimg_host.data() + off,
+                                    (size_t)6 * o.aimg_bytes, cudaMemcpyHostToDevice, st) !=
+                    cudaSuccess)
+                    return SYLV_ERR_CUDA;
+                off += (size_t)6 * o.aimg_bytes;
+            }
+        }
         p->evolve_t = t;
         p->evolve_ready = true;
     }
@@ -1628,13 +1687,42 @@ sylv_status sylv_evolve(sylv_plan_t p, double t, const void *B, const void *X0, 
     phase_begin(c, SYLV_PH_EVOLVE);
     if (launch_solve_init(c.flags, st) != cudaSuccess) return SYLV_ERR_CUDA;
     count(c);
-    // W = B + sigma X0 + sum_j A_j (x)_j X0  (residual passes with -A_j, -sigma)
-    const cd nsig = -p->sigma;
-    if (run_residual(c, B, X0, W, nullptr, p->nA64, &nsig) != cudaSuccess) return SYLV_ERR_CUDA;
-    // F = exp(t sigma) exp(t A_N) (x)_N ( ... exp(t A_1) (x)_1 W) - B, Eq. (C)
-    if (run_groups(c, p->egroups, true, 0, W, ELEM_C128, W, ELEM_C128, W, ELEM_C128, EPI_SUB,
-                   nullptr, p->E64, B, p->evolve_eps) != cudaSuccess)
-        return SYLV_ERR_CUDA;
+    if (p->oz) {
+        // the same two steps as digit products on the tensor cores: W = B + sum_j
+        // A_j (x)_j X0 (sigma in the first mode's digits), then F = E_N (x)_N ( ...
+        // E_1 (x)_1 W) - B one mode at a time, in place on W
+        const int64_t cnt = p->ntot * p->nrhs;
+        void *Rdf = (char *)ws + p->off_R;
+        const size_t np = p->ozpasses.size();
+        if (launch_maxabs(X0, cnt, c.flags, p->num_sms, st) != cudaSuccess) return SYLV_ERR_CUDA;
+        count(c);
+        for (size_t k = 0; k < np; ++k) {
+            const auto &o = p->ozpasses[k];
+            if (run_oz_pass(c, k, o.aimg, o.eA, X0, B, Rdf, Rdf, W,
+                            k == 0 ? OZ_IN_B : OZ_IN_PAIRS,
+                            k + 1 == np ? OZ_OUT_C128 : OZ_OUT_PAIRS, 1, 1.f, nullptr) != cudaSuccess)
+                return SYLV_ERR_CUDA;
+        }
+        for (size_t k = 0; k < np; ++k) {
+            const auto &o = p->ozpasses[k];
+            if (launch_maxabs(W, cnt, c.flags, p->num_sms, st) != cudaSuccess)
+                return SYLV_ERR_CUDA;
+            count(c);
+            if (run_oz_pass(c, k, o.eimg, o.eE, W, B, nullptr, nullptr, W,
+                            k + 1 == np ? OZ_IN_B : OZ_IN_ZERO, OZ_OUT_C128, 1, -1.f,
+                            nullptr) != cudaSuccess)
+                return SYLV_ERR_CUDA;
+        }
+    } else {
+        // W = B + sigma X0 + sum_j A_j (x)_j X0  (residual passes with -A_j, -sigma)
+        const cd nsig = -p->sigma;
+        if (run_residual(c, B, X0, W, nullptr, p->nA64, &nsig) != cudaSuccess)
+            return SYLV_ERR_CUDA;
+        // F = exp(t sigma) exp(t A_N) (x)_N ( ... exp(t A_1) (x)_1 W) - B, Eq. (C)
+        if (run_groups(c, p->egroups, true, 0, W, ELEM_C128, W, ELEM_C128, W, ELEM_C128, EPI_SUB,
+                       nullptr, p->E64, B, p->evolve_eps) != cudaSuccess)
+            return SYLV_ERR_CUDA;
+    }
     phase_end(c);
     // sum_j A_j (x)_j X(t) = F, Eq. (sylvesterNDC)
     int launches = 0;

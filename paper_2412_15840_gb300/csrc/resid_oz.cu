@@ -21,9 +21,18 @@
 //     result from R kept as FP32 pairs (hi, lo).
 // Digit pairs with t + u > 5 are dropped (< 2^-45 relative).  The scalar sigma
 // of the singleton modes is folded into the first mode's digits (A_1 + sigma I).
-// The first pass splits B into FP32 pairs by integer operations, so no pass
-// issues FP64 arithmetic; the last pass rounds R to complex64, the input of the
-// correction solve.
+//
+// The base an update is added to and the form of its result are runtime modes,
+// so one kernel serves every pass of the residual and of the Theorem 1 evolve:
+//   in:  OZ_IN_B      bsign * B, split into FP32 pairs by integer operations
+//                     (no FP64 arithmetic in the pass);
+//        OZ_IN_PAIRS  the FP32 pairs the previous pass wrote;
+//        OZ_IN_ZERO   nothing (a plain product A (x)_j X);
+//   out: OZ_OUT_PAIRS FP32 pairs for the next pass;
+//        OZ_OUT_C64   complex64 (the residual, input of the correction solve);
+//        OZ_OUT_C128  complex128 (W = B + sum_j A_j (x)_j X0 and the exp(t A_j)
+//                     products of the evolve, whose inputs are complex128).
+// `neg` chooses base - A (x)_j X (the residual) or base + A (x)_j X.
 //
 // Tiles follow the tensor-core transform pass: 64 consecutive rows of the
 // flattened (l, r) index for a later mode (M1 = 0), 64 consecutive columns for
@@ -32,6 +41,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "cplx.cuh"
@@ -117,13 +127,17 @@ __device__ __forceinline__ void df_add(float &h, float &l, float bh, float bl) {
 
 }  // namespace
 
-template <int M1, int FIRST, int LAST>
+template <int M1>
 __global__ void __launch_bounds__(OZ_THREADS, 1) k_resid_oz(const __grid_constant__ OzArgs a) {
     const double2 *Xg = reinterpret_cast<const double2 *>(a.X);
     const double2 *Bg = reinterpret_cast<const double2 *>(a.B);
     const float4 *Rin = reinterpret_cast<const float4 *>(a.Rin);
     float4 *Rout = reinterpret_cast<float4 *>(a.Rout);
     float2 *Rc64 = reinterpret_cast<float2 *>(a.Rc64);
+    double2 *Rc128 = reinterpret_cast<double2 *>(a.Rc64);
+    // operand read by the epilogue, its sign, and the output format (see OzArgs)
+    const int in_mode = a.in_mode, out_mode = a.out_mode;
+    const float vsign = a.neg ? 1.f : -1.f;       // R = base - value, or base + value
     extern __shared__ __align__(128) unsigned char sm[];
     __shared__ __align__(8) uint64_t mbar_a;
     __shared__ __align__(8) uint64_t mbar_mma;
@@ -285,9 +299,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_resid_oz(const __grid_constan
             for (int i0 = 8 * quarter; i0 < n; i0 += 32)
                 for (int t2 = 0; t2 < 4; ++t2, ++slot) {
                     const int i = i0 + 2 * t2 + cc;
-                    if (!live || i >= n) continue;
+                    if (!live || i >= n || in_mode == OZ_IN_ZERO) continue;
                     const int64_t g = gidx(r, p0, pl, i);
-                    const void *src = FIRST ? (const void *)(Bg + g) : (const void *)(Rin + g);
+                    const void *src = in_mode == OZ_IN_B ? (const void *)(Bg + g)
+                                                          : (const void *)(Rin + g);
                     cp_async16(Rs + ((size_t)slot * OZ_THREADS + tid) * 16, src);
                 }
             asm volatile("cp.async.commit_group;" ::: "memory");
@@ -332,25 +347,26 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_resid_oz(const __grid_constan
                 if (!live || i >= n) continue;
                 const int64_t g = gidx(r, p0, pl, i);
                 const unsigned char *sv = Rs + ((size_t)slot * OZ_THREADS + tid) * 16;
-                if (FIRST) {
-                    // R = B - A (x) X in FP32 pairs (sigma is folded into the first
-                    // mode's digits of A)
+                // base: B (FP64, split into FP32 pairs by integer operations; sigma is
+                // folded into the first mode's digits), R pairs, or zero
+                float xr = 0.f, lr = 0.f, xi = 0.f, li = 0.f;
+                if (in_mode == OZ_IN_B) {
                     const double2 bv = *reinterpret_cast<const double2 *>(sv);
-                    float xr, lr, xi, li;
                     split_double(bv.x, xr, lr);
                     split_double(bv.y, xi, li);
-                    df_add(xr, lr, -reh, -rel);
-                    df_add(xi, li, -imh, -iml);
-                    if (LAST) Rc64[g] = make_float2(xr + lr, xi + li);
-                    else Rout[g] = make_float4(xr, xi, lr, li);
-                } else {
+                    xr *= a.bsign; lr *= a.bsign; xi *= a.bsign; li *= a.bsign;
+                } else if (in_mode == OZ_IN_PAIRS) {
                     const float4 rv = *reinterpret_cast<const float4 *>(sv);
-                    float xr = rv.x, lr = rv.z, xi = rv.y, li = rv.w;
-                    df_add(xr, lr, -reh, -rel);
-                    df_add(xi, li, -imh, -iml);
-                    if (LAST) Rc64[g] = make_float2(xr + lr, xi + li);
-                    else Rout[g] = make_float4(xr, xi, lr, li);
+                    xr = rv.x; xi = rv.y; lr = rv.z; li = rv.w;
                 }
+                df_add(xr, lr, vsign * reh, vsign * rel);
+                df_add(xi, li, vsign * imh, vsign * iml);
+                if (out_mode == OZ_OUT_C64)
+                    Rc64[g] = make_float2(xr + lr, xi + li);
+                else if (out_mode == OZ_OUT_C128)
+                    Rc128[g] = make_double2((double)xr + (double)lr, (double)xi + (double)li);
+                else
+                    Rout[g] = make_float4(xr, xi, lr, li);
             }
         }
     };
@@ -382,41 +398,42 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_resid_oz(const __grid_constan
     if (warp == 0) tmem_dealloc(tmem, (uint32_t)a.tmem_cols);
 }
 
-cudaError_t launch_resid_oz(const OzArgs &a, int first, int last, int grid, size_t smem,
-                            cudaStream_t st) {
+cudaError_t launch_resid_oz(const OzArgs &a, int grid, size_t smem, cudaStream_t st) {
     if (a.n < 8 || a.n > 64) return cudaErrorInvalidValue;
-#define SYLV_OZ_LAUNCH(m1, f, l) k_resid_oz<m1, f, l><<<grid, OZ_THREADS, smem, st>>>(a)
-    if (a.mode1) {
-        if (first && last) SYLV_OZ_LAUNCH(1, 1, 1);
-        else if (first) SYLV_OZ_LAUNCH(1, 1, 0);
-        else if (last) SYLV_OZ_LAUNCH(1, 0, 1);
-        else SYLV_OZ_LAUNCH(1, 0, 0);
-    } else {
-        if (first && last) SYLV_OZ_LAUNCH(0, 1, 1);
-        else if (first) SYLV_OZ_LAUNCH(0, 1, 0);
-        else if (last) SYLV_OZ_LAUNCH(0, 0, 1);
-        else SYLV_OZ_LAUNCH(0, 0, 0);
-    }
-#undef SYLV_OZ_LAUNCH
+    if (a.mode1)
+        k_resid_oz<1><<<grid, OZ_THREADS, smem, st>>>(a);
+    else
+        k_resid_oz<0><<<grid, OZ_THREADS, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <int M1, int F, int L>
-static cudaError_t oz_attr() {
-    return cudaFuncSetAttribute(k_resid_oz<M1, F, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                TC_SMEM_MAX);
+// max(|re|, |im|) of a complex128 tensor into flags->xlast (float bits): the
+// digit scale of the next pass's input
+__global__ void k_maxabs(const double2 *x, int64_t count, DevFlags *flags) {
+    float m = 0.f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, cabsmax(x[i]));
+    m = warp_max(m);
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(&flags->xlast, m);
+}
+
+cudaError_t launch_maxabs(const void *x, int64_t count, DevFlags *flags, int num_sms,
+                          cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(&flags->xlast, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess || count <= 0) return e;
+    const int64_t blocks = std::min<int64_t>((count + 255) / 256, (int64_t)num_sms * 8);
+    k_maxabs<<<(unsigned)blocks, 256, 0, st>>>(reinterpret_cast<const double2 *>(x), count,
+                                               flags);
+    return cudaGetLastError();
 }
 
 cudaError_t resid_oz_init_attrs() {
-    cudaError_t e;
-    if ((e = oz_attr<0, 0, 0>()) != cudaSuccess) return e;
-    if ((e = oz_attr<0, 0, 1>()) != cudaSuccess) return e;
-    if ((e = oz_attr<0, 1, 0>()) != cudaSuccess) return e;
-    if ((e = oz_attr<0, 1, 1>()) != cudaSuccess) return e;
-    if ((e = oz_attr<1, 0, 0>()) != cudaSuccess) return e;
-    if ((e = oz_attr<1, 0, 1>()) != cudaSuccess) return e;
-    if ((e = oz_attr<1, 1, 0>()) != cudaSuccess) return e;
-    return oz_attr<1, 1, 1>();
+    cudaError_t e = cudaFuncSetAttribute(k_resid_oz<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         TC_SMEM_MAX);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_resid_oz<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                TC_SMEM_MAX);
 }
 
 }  // namespace sylv

@@ -150,9 +150,13 @@ struct TCArgs {
 struct OzArgs {
     const void *X;                // complex128
     const void *B;                // complex128 (first pass)
-    const void *Rin;              // R as FP32 pairs (re hi, im hi, re lo, im lo), later passes
-    void *Rout;                   // the same, all passes but the last
-    void *Rc64;                   // R rounded to complex64, last pass
+    const void *Rin;              // R as FP32 pairs (re hi, im hi, re lo, im lo)
+    void *Rout;                   // output as FP32 pairs (out_mode OZ_OUT_PAIRS)
+    void *Rc64;                   // output as complex64 or complex128 (OZ_OUT_C64 / _C128)
+    int in_mode;                  // base of the update: OZ_IN_B (bsign * B), OZ_IN_PAIRS, OZ_IN_ZERO
+    int out_mode;                 // OZ_OUT_PAIRS, OZ_OUT_C64, OZ_OUT_C128
+    int neg;                      // 0: out = base - A (x)_j X; 1: out = base + A (x)_j X
+    float bsign;                  // +1 or -1
     const unsigned char *aimg;    // 6 digit images of [Re A^T | Im A^T] (B operand layout)
     int n, Kp, Np;                // mode size, K padded to 16, N = 2n padded to 16
     int mode1;                    // 1: first mode (tiles of 64 columns)
@@ -167,9 +171,13 @@ struct OzArgs {
     const int *done;
 };
 
+enum { OZ_IN_PAIRS = 0, OZ_IN_B = 1, OZ_IN_ZERO = 2 };
+enum { OZ_OUT_PAIRS = 0, OZ_OUT_C64 = 1, OZ_OUT_C128 = 2 };
+
 #ifdef __CUDACC__
-cudaError_t launch_resid_oz(const OzArgs &a, int first, int last, int grid, size_t smem,
-                            cudaStream_t st);
+cudaError_t launch_resid_oz(const OzArgs &a, int grid, size_t smem, cudaStream_t st);
+cudaError_t launch_maxabs(const void *x, int64_t count, DevFlags *flags, int num_sms,
+                          cudaStream_t st);
 cudaError_t resid_oz_init_attrs();
 cudaError_t launch_modeprod_tc(int epi, const TCArgs &a, int grid, size_t smem, cudaStream_t st);
 cudaError_t modeprod_tc_init_attrs();

@@ -51,9 +51,11 @@ def test_emu_matches_oracle(shape, nrhs, on_tc):
 def test_emu_residual_accuracy_matches_fp64_residual():
     # one refinement step with each residual: the corrections agree to the
     # residuals' accuracy, far below the FP32 solve's error
+    # (the default rtol keeps the conditioning guard satisfied; max_refine = 1 stops
+    # both paths after one correction)
     p = si.random_problem((64, 32, 16), 1, seed=21)
-    Xe, ie = _solve(p.A, p.B, max_refine=1, rtol=1e-30)
-    plan = Plan(A=p.A, nrhs=1, prec="mixed", max_refine=1, rtol=1e-30)
+    Xe, ie = _solve(p.A, p.B, max_refine=1)
+    plan = Plan(A=p.A, nrhs=1, prec="mixed", max_refine=1)
     Xm, im = plan.solve(to_device(p.B), info=True)
     Xm = from_device(Xm, p.B.shape)
     Xo = oracle.solve(p.A, p.B)
@@ -109,3 +111,17 @@ def test_emu_ill_conditioned_keeps_the_fp64_residual():
     X, info = _solve(A, B, max_refine=8)
     assert info["status"] == 0 and not info["tensor_core_residual"]
     assert oracle.rel_err(X, oracle.solve(A, B)) < 1e-10
+
+
+@pytest.mark.parametrize("shape,nrhs,t", [((64, 24, 9), 1, 0.3), ((64, 1, 16), 4, 0.7),
+                                          ((48, 16, 8), 2, 1.1)])
+def test_emu_evolve_on_the_tensor_cores(shape, nrhs, t):
+    # Theorem 1 with the right-hand side F formed by digit products (W = B + sum_j
+    # A_j (x)_j X0, then the exp(t A_j) products), then the emulated-residual solve
+    p = si.random_problem(shape, nrhs, seed=40 + sum(shape))
+    X0 = si.initial_state(p.shape, nrhs, seed=41)
+    plan = Plan(A=p.A, nrhs=nrhs, prec="mixed_emu")
+    X, info = plan.evolve(t, to_device(p.B), to_device(X0), info=True)
+    assert info["status"] == 0 and info["tensor_core_residual"]
+    ref = oracle.evolve(p.A, p.B, X0, t)
+    assert oracle.rel_err(from_device(X, p.B.shape), ref) < 1e-10
