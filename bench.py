@@ -537,7 +537,9 @@ def main():
     solves = max(1, phases_m["solves"])
     iters = max(1, info_m["refine_iters"])
     sum_n = sum(n for n in SHAPE if n > 1)
-    res_flops_per_pass = 8.0 * entries * sum_n            # one residual over all modes
+    # one residual over all modes: three FP64 FMAs (6 flops) per entry, mode and k
+    # (Gauss's three-multiplication complex product)
+    res_flops_per_pass = 6.0 * entries * sum_n
     res_ms = phases_m["ms"]["residual"] / solves          # per solve (all iterations)
     achieved = res_flops_per_pass * iters / (res_ms * 1e-3) / 1e12 if res_ms > 0 else None
     traffic = TRAFFIC["bytes_per_launch"] if TRAFFIC["kernels_sha"] == kernels_sha() else None
@@ -560,6 +562,7 @@ def main():
                      "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
                      "traffic": traffic, "traffic_unit": "bytes per launch",
                      "algorithmic_bytes_per_launch": 3 * nbytes,
+                     "flops_note": "6 sum(n_j) FP64 flops per entry (3 FMAs per complex term)",
                      "peak_note": "FP64 FMA pipe derived: 152 SMs x 2 FMA/clk x 2 FLOP x 2070 MHz"},
         "phases_ms_per_solve": {
             "mixed": {k: v / solves for k, v in phases_m["ms"].items()},

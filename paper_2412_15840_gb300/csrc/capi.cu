@@ -327,7 +327,7 @@ sylv_status make_groups(const sylv_plan_s &p, bool fp64, bool composition, int g
         g.first = 0; g.count = 0; g.L = 1; g.P = 1; g.R = tot;
         choose_tile(1, 1, tot, Et, Eh, g.Lt, g.Rt);
         g.tilesL = 1;
-        g.smem = (size_t)(g.Lt * g.Rt) * esz;
+        g.smem = (size_t)(g.Lt * g.Rt) * (esz + ((!composition && fp64) ? 8 : 0));
         out.push_back(g);
         return SYLV_OK;
     }
@@ -360,7 +360,10 @@ sylv_status make_groups(const sylv_plan_s &p, bool fp64, bool composition, int g
         if (!choose_tile(g.L, g.P, g.R, Et, Eh, g.Lt, g.Rt)) return SYLV_ERR_SHAPE;
         g.tilesL = (g.L + g.Lt - 1) / g.Lt;
         int64_t E = (int64_t)g.Lt * g.P * g.Rt;
+        // composition: two tiles (ping-pong); residual: the tile and its
+        // re + im plane (FP64 only); otherwise one tile
         g.smem = (size_t)(E * esz * ((composition && g.count > 1) ? 2 : 1));
+        if (!composition && fp64) g.smem += (size_t)E * 8;
         if (g.smem > 200 * 1024) return SYLV_ERR_SHAPE;
         out.push_back(g);
         j += g.count;
@@ -672,7 +675,8 @@ cudaError_t run_groups(Ctx &c, const std::vector<Group> &gs, bool fp64, int whic
 }
 
 // R = B - sigma X - sum_j M_j (x)_j X over the FP64 residual passes, M_j = A_j
-// (or the given per-mode matrices, with the given sigma)
+// (or the given per-mode matrices, with the given sigma; each matrix carries the
+// plane re + im after its entries)
 cudaError_t run_residual(Ctx &c, const void *B, const void *X, void *R, const int *done,
                          const void *const *mats = nullptr, const cd *sig = nullptr) {
     sylv_plan_s *p = c.p;
@@ -1213,10 +1217,12 @@ sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t 
     auto reserve = [&](size_t bytes) { off = align256(off); offs.push_back(off); off += bytes; };
     for (int j = 0; j < p->Nm; ++j) {
         size_t nn = (size_t)(p->n[j] * p->n[j]);
-        reserve(nn * 16); reserve(nn * 16); reserve(nn * 16); reserve(nn * 16);
+        // the FP64 product matrices (U_j^*, U_j, A_j, -A_j, exp(t A_j)) carry a
+        // plane re + im after the complex entries (three-multiplication products)
+        reserve(nn * 24); reserve(nn * 24); reserve(nn * 24); reserve(nn * 16);
         reserve((size_t)p->n[j] * 16);
         reserve(nn * 8); reserve(nn * 8); reserve(nn * 8);
-        reserve(nn * 16); reserve(nn * 16);              // -A_j, exp(t A_j)
+        reserve(nn * 24); reserve(nn * 24);              // -A_j, exp(t A_j)
     }
     reserve(3 * sizeof(unsigned long long));
     const size_t oz_first = offs.size();
@@ -1282,6 +1288,12 @@ sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t 
         p->T32[j] = base + offs[oi + 7];
         double *na64 = (double *)(host.data() + offs[oi + 8]);
         for (size_t k = 0; k < (size_t)(2 * nj * nj); ++k) na64[k] = -a64[k];
+        for (size_t k = 0; k < (size_t)(nj * nj); ++k) {
+            uh64[2 * nj * nj + k] = uh64[2 * k] + uh64[2 * k + 1];
+            u64[2 * nj * nj + k] = u64[2 * k] + u64[2 * k + 1];
+            a64[2 * nj * nj + k] = a64[2 * k] + a64[2 * k + 1];
+            na64[2 * nj * nj + k] = na64[2 * k] + na64[2 * k + 1];
+        }
         p->nA64[j] = base + offs[oi + 8];
         p->E64[j] = base + offs[oi + 9];
         oi += 10;
@@ -1628,8 +1640,9 @@ sylv_status sylv_evolve(sylv_plan_t p, double t, const void *B, const void *X0, 
     cudaStream_t st = (cudaStream_t)stream;
     // exp(t A_j) on the host (Pade scaling and squaring), uploaded in stream order
     if (!p->evolve_ready || p->evolve_t != t) {
+        // per mode: the complex entries, then the plane re + im
         size_t tot = 0;
-        for (int j = 0; j < p->Nm; ++j) tot += (size_t)(2 * p->n[j] * p->n[j]);
+        for (int j = 0; j < p->Nm; ++j) tot += (size_t)(3 * p->n[j] * p->n[j]);
         p->Ehost.assign(tot, 0.0);
         size_t o = 0;
         for (int j = 0; j < p->Nm; ++j) {
@@ -1640,13 +1653,16 @@ sylv_status sylv_evolve(sylv_plan_t p, double t, const void *B, const void *X0, 
                 tA[2 * k] = t * Aj[k].real();
                 tA[2 * k + 1] = t * Aj[k].imag();
             }
-            sylv_status s = expm_host(nj, tA.data(), p->Ehost.data() + o);
+            double *Ej = p->Ehost.data() + o;
+            sylv_status s = expm_host(nj, tA.data(), Ej);
             if (s != SYLV_OK) return s;
-            o += (size_t)(2 * nj * nj);
+            for (size_t k = 0; k < (size_t)(nj * nj); ++k)
+                Ej[2 * nj * nj + k] = Ej[2 * k] + Ej[2 * k + 1];
+            o += (size_t)(3 * nj * nj);
         }
         o = 0;
         for (int j = 0; j < p->Nm; ++j) {
-            const size_t bytes = (size_t)(p->n[j] * p->n[j]) * 16;
+            const size_t bytes = (size_t)(p->n[j] * p->n[j]) * 24;
             if (cudaMemcpyAsync(const_cast<void *>(p->E64[j]), p->Ehost.data() + o, bytes,
                                 cudaMemcpyHostToDevice, st) != cudaSuccess)
                 return SYLV_ERR_CUDA;
@@ -1666,7 +1682,7 @@ sylv_status sylv_evolve(sylv_plan_t p, double t, const void *B, const void *X0, 
                 const int64_t nj = o.n;
                 std::vector<cd> Em((size_t)(nj * nj));
                 size_t base = 0;
-                for (int q = 0; q < o.j; ++q) base += (size_t)(2 * p->n[q] * p->n[q]);
+                for (int q = 0; q < o.j; ++q) base += (size_t)(3 * p->n[q] * p->n[q]);
                 for (size_t k = 0; k < Em.size(); ++k)
                     Em[k] = cd(p->Ehost[base + 2 * k], p->Ehost[base + 2 * k + 1]) *
                             (o.j == 0 ? p->evolve_eps : cd(1.0));

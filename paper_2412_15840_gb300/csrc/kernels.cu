@@ -70,6 +70,59 @@ __device__ __forceinline__ int mode_rows(const C2 *__restrict__ src, const C2 *_
     for (int r = 0; r < RB; ++r) acc[r] = c[r];
     return aa + inner * (i0 + nm * bb);
 }
+// FP64 variant of mode_rows by Gauss's three-multiplication complex product:
+// with s = re + im of the matrix entry (the plane stored after the matrix) and
+// sx = xr + xi (one addition per loaded entry, shared by the RB rows),
+//   re = sum mr xr - sum mi xi,  im = sum s sx - sum mr xr - sum mi xi,
+// three FP64 FMAs per (i, k) instead of four.
+template <int RB>
+__device__ __forceinline__ int mode_rows_3m(const double2 *__restrict__ src,
+                                            const double2 *__restrict__ M, int nm, int inner,
+                                            int w, double2 *acc) {
+    const int aa = w % inner;
+    const int rest = w / inner;
+    const int ng = nm / RB;
+    const int ig = rest % ng;
+    const int bb = rest / ng;
+    const int i0 = ig * RB;
+    const double2 *col = src + aa + bb * inner * nm;
+    const double *MS = reinterpret_cast<const double *>(M + nm * nm);
+    double p1[RB], p2[RB], p3[RB];
+#pragma unroll
+    for (int r = 0; r < RB; ++r) p1[r] = p2[r] = p3[r] = 0.0;
+    const double2 *mk = M + i0;
+    const double *sk = MS + i0;
+    for (int k = 0; k < nm; ++k) {
+        const double2 x = col[k * inner];
+        const double sx = x.x + x.y;
+        double2 m[RB];
+        double s[RB];
+#pragma unroll
+        for (int r = 0; r < RB; ++r) m[r] = __ldg(mk + r);
+        if (RB == 1) {
+            s[0] = __ldg(sk);
+        } else {
+#pragma unroll
+            for (int r = 0; r < RB; r += 2) {
+                const double2 q = __ldg(reinterpret_cast<const double2 *>(sk + r));
+                s[r] = q.x;
+                s[r + 1] = q.y;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < RB; ++r) {
+            p1[r] = fma(m[r].x, x.x, p1[r]);
+            p2[r] = fma(m[r].y, x.y, p2[r]);
+            p3[r] = fma(s[r], sx, p3[r]);
+        }
+        mk += nm;
+        sk += nm;
+    }
+#pragma unroll
+    for (int r = 0; r < RB; ++r) acc[r] = make_double2(p1[r] - p2[r], (p3[r] - p1[r]) - p2[r]);
+    return aa + inner * (i0 + nm * bb);
+}
+
 template <typename real, typename Tin, typename Tout, int EPI>
 __global__ void __launch_bounds__(256) k_modeprod(const __grid_constant__ MPArgs a) {
     using C2 = typename C2T<real>::type;
@@ -97,31 +150,50 @@ __global__ void __launch_bounds__(256) k_modeprod(const __grid_constant__ MPArgs
         C2 v = czero<C2>();
         if (l < lv && r < rv) v = to_c(in[(l0 + l) + L * ((int64_t)p + a.P * (r0 + r))], real());
         buf0[t] = v;
+        if (EPI == EPI_RESID) reinterpret_cast<real *>(buf1)[t] = v.x + v.y;
     }
     __syncthreads();
 
     float nd = 0.f, nx = 0.f;
     const int G = a.G;
     if (EPI == EPI_RESID) {
-        // sum over the group's modes of A_m (x)_m X, all read from buf0
+        // sum over the group's modes of A_m (x)_m X, all read from buf0, by
+        // Gauss's three-multiplication form of the complex product:
+        //   Re = sum ar xr - sum ai xi,  Im = sum (ar + ai)(xr + xi) - sum ar xr - sum ai xi
+        // with ar + ai stored after each matrix and xr + xi staged beside the
+        // tile, so every (i, k) term costs three FP64 FMAs instead of four.
+        const real *bufS = reinterpret_cast<const real *>(buf1);
         for (int t = threadIdx.x; t < E; t += blockDim.x) {
             int l = t % Lt;
             int rest = t / Lt;
             int p = rest % P;
             int r = rest / P;
-            C2 acc = czero<C2>();
+            real p1 = 0, p2 = 0, p3 = 0;
             int inner = Lt;
             for (int m = 0; m < G; ++m) {
                 const int nm = a.gn[m];
                 const C2 *M = reinterpret_cast<const C2 *>(a.mats[m]);
+                const real *MS = reinterpret_cast<const real *>(M + nm * nm);
                 int aa = t % inner;
                 int rr = t / inner;
                 int i = rr % nm;
                 int bb = rr / nm;
-                const C2 *src = buf0 + aa + (int64_t)bb * inner * nm;
-                for (int k = 0; k < nm; ++k) cmac(acc, __ldg(M + i + k * nm), src[k * inner]);
+                const int64_t o = aa + (int64_t)bb * inner * nm;
+                const C2 *src = buf0 + o;
+                const real *srcS = bufS + o;
+                for (int k = 0; k < nm; ++k) {
+                    const C2 am = __ldg(M + i + k * nm);
+                    const real as = __ldg(MS + i + k * nm);
+                    const C2 x = src[k * inner];
+                    p1 = fma(am.x, x.x, p1);
+                    p2 = fma(am.y, x.y, p2);
+                    p3 = fma(as, srcS[k * inner], p3);
+                }
                 inner *= nm;
             }
+            C2 acc;
+            acc.x = p1 - p2;
+            acc.y = (p3 - p1) - p2;
             if (l < lv && r < rv) {
                 int64_t g = (l0 + l) + L * ((int64_t)p + a.P * (r0 + r));
                 double2 *Rp = reinterpret_cast<double2 *>(a.out);
@@ -194,9 +266,15 @@ __global__ void __launch_bounds__(256) k_modeprod(const __grid_constant__ MPArgs
         for (int w = threadIdx.x; w < W; w += blockDim.x) {
             C2 acc[4];
             int tb;
-            if (rb == 4) tb = mode_rows<4>(src, M, nm, inner, w, acc);
-            else if (rb == 2) tb = mode_rows<2>(src, M, nm, inner, w, acc);
-            else tb = mode_rows<1>(src, M, nm, inner, w, acc);
+            if constexpr (sizeof(real) == 8) {
+                if (rb == 4) tb = mode_rows_3m<4>(src, M, nm, inner, w, acc);
+                else if (rb == 2) tb = mode_rows_3m<2>(src, M, nm, inner, w, acc);
+                else tb = mode_rows_3m<1>(src, M, nm, inner, w, acc);
+            } else {
+                if (rb == 4) tb = mode_rows<4>(src, M, nm, inner, w, acc);
+                else if (rb == 2) tb = mode_rows<2>(src, M, nm, inner, w, acc);
+                else tb = mode_rows<1>(src, M, nm, inner, w, acc);
+            }
             for (int r = 0; r < rb; ++r) {
                 const int t = tb + r * inner;
                 if (!last) dst[t] = acc[r];
