@@ -308,6 +308,19 @@ sylv_status sylv_plan_timing(sylv_plan_t plan, sylv_timing *out, int reset);
 sylv_status sylv_schur(int64_t n, const double *A, double *Q, double *T);
 
 /*
+ * Host-only helper (no GPU needed): real Schur decomposition A = Q T Q^T of one
+ * n x n real (float64) matrix, the factorisation the real-arithmetic variant
+ * uses: Q orthogonal, T quasi-upper-triangular with 1 x 1 blocks for real
+ * eigenvalues and 2 x 2 blocks for complex-conjugate pairs (Golub & Van Loan,
+ * ch. 7: Hessenberg reduction, Francis double-shift QR).  Every 2 x 2 block
+ * starts at an even index (T[k+1, k] != 0 only for even k), reached by direct
+ * swaps of adjacent blocks (Bai & Demmel 1993).  A, Q, T column-major, n*n
+ * doubles each.  SYLV_ERR_SCHUR if QR does not converge or a swap is
+ * ill-conditioned; SYLV_ERR_INVALID_ARG for n < 1 or non-finite entries.
+ */
+sylv_status sylv_schur_real(int64_t n, const double *A, double *Q, double *T);
+
+/*
  * sylv_expm -- host-only matrix exponential E = exp(M) of an n x n complex128
  * matrix (column-major, 1 <= n <= 1024), by scaling and squaring with the
  * [13/13] Pade approximant (Higham, SIAM J. Matrix Anal. Appl. 26(4), 2005).

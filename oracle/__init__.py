@@ -14,7 +14,12 @@ invariant, the nested-loop Algorithm 1, and planted mistakes.  The ODE solution 
 Theorem 1 (`evolve`) is pinned against the exponential of the augmented
 Kronecker-sum matrix, the scalar closed form for diagonal operators, a
 fourth-order Runge-Kutta integration (the experiment of Section 5.2), its
-t = 0 and steady-state limits, and planted mistakes.
+t = 0 and steady-state limits, and planted mistakes.  The real-arithmetic
+variant (`real_variant`: real Schur factors, quasi-triangular sweep) is pinned
+in tests/test_oracle_real.py against the dense Kronecker-sum solve (of A_j and
+of the T_j), the classical 2-D Sylvester solver, the complex oracle's solution
+of the same real problem, orthogonality of the transforms, and planted
+mistakes (block coupling dropped, factor transposed).
 """
 from .bartels_stewart import (  # noqa: F401
     linear_index,

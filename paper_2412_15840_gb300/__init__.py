@@ -17,10 +17,11 @@ from .binding import (  # noqa: F401
     from_device,
     lib,
     schur,
+    schur_real,
     solve_batched,
     to_device,
     workspace_size_batched,
 )
 
-__all__ = ["Plan", "SylvError", "schur", "expm", "solve_batched", "workspace_size_batched",
+__all__ = ["Plan", "SylvError", "schur", "schur_real", "expm", "solve_batched", "workspace_size_batched",
            "to_device", "from_device", "lib", "EXPORTED", "PHASES"]

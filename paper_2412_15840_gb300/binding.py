@@ -35,7 +35,7 @@ EXPORTED = ("sylv_plan_create", "sylv_plan_destroy", "sylv_workspace_size", "syl
             "sylv_back", "sylv_residual", "sylv_plan_factors", "sylv_plan_set_timing",
             "sylv_plan_timing", "sylv_schur", "sylv_status_string", "sylv_version",
             "sylv_sweep_static", "sylv_plan_autotune", "sylv_evolve_workspace_size",
-            "sylv_evolve", "sylv_expm")
+            "sylv_evolve", "sylv_expm", "sylv_schur_real")
 
 
 class SylvError(RuntimeError):
@@ -121,6 +121,8 @@ def _lib():
         L.sylv_plan_timing.argtypes = [vp, ctypes.POINTER(Timing), ctypes.c_int]
         L.sylv_schur.restype = st
         L.sylv_schur.argtypes = [ctypes.c_int64, vp, vp, vp]
+        L.sylv_schur_real.restype = st
+        L.sylv_schur_real.argtypes = [ctypes.c_int64, vp, vp, vp]
         L.sylv_expm.restype = st
         L.sylv_expm.argtypes = [ctypes.c_int64, vp, vp]
         L.sylv_evolve_workspace_size.restype = st
@@ -160,6 +162,18 @@ def schur(A) -> tuple:
     Q = np.zeros((n, n), dtype=np.complex128, order="F")
     T = np.zeros((n, n), dtype=np.complex128, order="F")
     _check(_lib().sylv_schur(n, a.ctypes.data, Q.ctypes.data, T.ctypes.data), "sylv_schur")
+    return Q, T
+
+
+def schur_real(A) -> tuple:
+    """Host real Schur A = Q T Q^T computed by the library (no GPU needed): T
+    quasi-upper-triangular, its 2 x 2 blocks at even offsets."""
+    a = np.asfortranarray(np.asarray(A, dtype=np.float64).reshape(np.shape(A) or (1, 1)))
+    n = a.shape[0]
+    Q = np.zeros((n, n), dtype=np.float64, order="F")
+    T = np.zeros((n, n), dtype=np.float64, order="F")
+    _check(_lib().sylv_schur_real(n, a.ctypes.data, Q.ctypes.data, T.ctypes.data),
+           "sylv_schur_real")
     return Q, T
 
 

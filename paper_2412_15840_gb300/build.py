@@ -21,7 +21,7 @@ BUILD = os.path.join(PKG, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["kernels.cu", "sweep.cu", "modeprod_tc.cu", "resid_oz.cu", "capi.cu", "schur.cpp",
-           "expm.cpp"]
+           "schur_real.cpp", "expm.cpp"]
 HEADERS = ["sylv_internal.h", "cplx.cuh", "tc_ptx.cuh", os.path.join("..", "..", "include", "sylv.h")]
 
 

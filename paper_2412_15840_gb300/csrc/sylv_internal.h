@@ -23,6 +23,7 @@ constexpr int SWEEP_BMAX = 64; // automatic tile extents stay <= 64 per mode, so
 
 sylv_status schur_host(int64_t n, const double *A, double *Q, double *T);
 sylv_status expm_host(int64_t n, const double *M, double *E);
+sylv_status schur_real_host(int64_t n, const double *A, double *Q, double *T);
 
 // Device-side control block at the start of every workspace.
 struct DevFlags {

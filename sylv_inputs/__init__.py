@@ -21,7 +21,10 @@ Recipe (seed 0 unless stated):
   * the batched workload draws its 512 x 3 shapes with
     rng.integers(16, 97, size=(512, 3)) before any matrix;
   * the periodic advection-diffusion operator is 0.01*D2 + 0.5*D1 + I with
-    centred differences on x_m = 2*pi*m/n, h = 2*pi/n.
+    centred differences on x_m = 2*pi*m/n, h = 2*pi/n;
+  * real problems (the real-arithmetic variant): A = randn(n,n)/sqrt(n) +
+    shift*I drawn mode by mode, singleton modes [1.5], B real unit-variance
+    Gaussian drawn after every operator in chunks of 2**26 entries.
 """
 from __future__ import annotations
 
@@ -99,6 +102,39 @@ def random_problem(shape: Sequence[int], nrhs: int = 1, seed: int = 0,
             A.append(gaussian_operator(rng, int(n), shift, scale))
     B = complex_gaussian(rng, tuple(shape) + (nrhs,))
     return Problem(A=A, B=B, name=name or f"random{tuple(shape)}x{nrhs}")
+
+
+def real_gaussian(rng: np.random.Generator, shape: Sequence[int]) -> np.ndarray:
+    """Unit-variance real Gaussian tensor in Fortran order, drawn in chunks."""
+    total = int(np.prod(shape, dtype=np.int64))
+    out = np.empty(total, dtype=np.float64)
+    for start in range(0, total, CHUNK):
+        stop = min(total, start + CHUNK)
+        out[start:stop] = rng.standard_normal(stop - start)
+    return out.reshape(tuple(shape), order="F")
+
+
+def random_real_problem(shape: Sequence[int], nrhs: int = 1, seed: int = 0,
+                        shift: float = 3.0, scale: Optional[float] = None,
+                        singleton_value: float = 1.5, name: str = "") -> Problem:
+    """Real dense Gaussian operators randn/sqrt(n) + shift I and a real B."""
+    rng = np.random.default_rng(seed)
+    A = []
+    for n in shape:
+        if n == 1:
+            A.append(np.array([[float(singleton_value)]]))
+        else:
+            a = rng.standard_normal((int(n), int(n))) * (
+                1.0 / math.sqrt(n) if scale is None else scale)
+            a[np.diag_indices(int(n))] += shift
+            A.append(a)
+    B = real_gaussian(rng, tuple(shape) + (nrhs,))
+    return Problem(A=A, B=B, name=name or f"real{tuple(shape)}x{nrhs}")
+
+
+def real_cube_n64_N4(seed: int = 0) -> Problem:
+    """Real N=4, n=64: 16,777,216 entries (134 MB in float64)."""
+    return random_real_problem((64,) * 4, 1, seed, shift=3.0, name="real_N4_n64")
 
 
 def periodic_advdiff_operator(n: int, nu: float = 0.01, c: float = 0.5,

@@ -77,6 +77,94 @@ def test_host_schur_rejects_bad_input():
         pkg.schur(np.full((3, 3), np.nan + 0j))
 
 
+def _check_real_schur(A, Q, T, tol=1e-13):
+    n = A.shape[0]
+    assert Q.dtype == np.float64 and T.dtype == np.float64
+    assert np.abs(Q.T @ Q - np.eye(n)).max() < tol * max(1, n)
+    assert np.abs(Q @ T @ Q.T - A).max() < tol * max(1, n) * max(1.0, np.abs(A).max())
+    # quasi-triangular: nothing below the first subdiagonal; subdiagonal entries
+    # only at even k, never two in a row
+    assert np.abs(np.tril(T, -2)).max(initial=0.0) == 0.0
+    sub = np.diag(T, -1)
+    assert all(sub[k] == 0.0 for k in range(len(sub)) if k % 2 == 1)
+    # every 2 x 2 block holds a complex-conjugate pair (real pairs were split)
+    for k in range(0, len(sub)):
+        if sub[k] != 0.0:
+            a, b, c, d = T[k, k], T[k, k + 1], T[k + 1, k], T[k + 1, k + 1]
+            assert ((a - d) / 2) ** 2 + b * c < 0
+    # the eigenvalues of the blocks are those of A
+    ev = []
+    k = 0
+    while k < n:
+        if k + 1 < n and T[k + 1, k] != 0.0:
+            ev.extend(np.linalg.eigvals(T[k:k + 2, k:k + 2]))
+            k += 2
+        else:
+            ev.append(T[k, k])
+            k += 1
+    ref = np.sort_complex(np.linalg.eigvals(A))
+    assert np.abs(np.sort_complex(np.array(ev, dtype=complex)) - ref).max() < 1e-9 * max(
+        1.0, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("n,seed", [(1, 0), (2, 1), (3, 2), (5, 7), (8, 3), (19, 4), (64, 5),
+                                    (96, 6)])
+def test_host_real_schur_factorisation(n, seed):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((n, n)) / np.sqrt(n) + 3 * np.eye(n)
+    Q, T = pkg.schur_real(A)
+    _check_real_schur(A, Q, T)
+    # the number of complex pairs agrees with scipy's real Schur form
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    Ts, _ = scipy_linalg.schur(A, output="real")
+    assert np.count_nonzero(np.diag(T, -1)) == np.count_nonzero(np.abs(np.diag(Ts, -1)) > 0)
+
+
+def test_host_real_schur_structures():
+    # a rotation generator (only complex pairs), an already triangular matrix (no
+    # pairs), a companion matrix with a pair at an odd offset after QR, a Jordan
+    # block, and 2 x 2 matrices with real / complex eigenvalues
+    rot = np.kron(np.eye(3), np.array([[0.0, 1.0], [-1.0, 0.0]])) + 0.1 * np.triu(np.ones((6, 6)), 1)
+    comp = np.zeros((5, 5))
+    comp[0, :] = [-1.0, 2.0, -3.0, 0.5, -2.0]
+    comp[1:, :-1] = np.eye(4)
+    for A in (rot, np.triu(np.arange(1.0, 26.0).reshape(5, 5)), comp,
+              np.eye(6, k=1) + 2 * np.eye(6), np.array([[1.0, 2.0], [3.0, 4.0]]),
+              np.array([[1.0, -2.0], [3.0, 1.0]])):
+        Q, T = pkg.schur_real(A)
+        _check_real_schur(A, Q, T, tol=1e-12)
+
+
+def test_host_real_schur_moves_pairs_to_even_offsets():
+    # inputs already in real Schur form with pairs at odd offsets: QR deflates at
+    # once and only the block swaps can move the pairs
+    Tm = np.array([[5.0, 1.0, 2.0], [0.0, 1.0, 2.0], [0.0, -3.0, 1.0]])
+    Q, T = pkg.schur_real(Tm)
+    _check_real_schur(Tm, Q, T)
+    assert T[1, 0] != 0.0 and T[2, 1] == 0.0
+    assert abs(T[2, 2] - 5.0) < 1e-12
+    M = np.zeros((7, 7))
+    M[0, 0], M[3, 3], M[6, 6] = 2.0, -1.0, 4.0
+    M[1:3, 1:3] = [[1.0, 2.0], [-3.0, 1.0]]
+    M[4:6, 4:6] = [[0.0, 1.0], [-1.0, 0.0]]
+    M += 0.3 * np.triu(np.ones((7, 7)), 1)
+    Q, T = pkg.schur_real(M)
+    _check_real_schur(M, Q, T)
+    assert [k for k in range(6) if T[k + 1, k] != 0.0] == [0, 4]
+    # the same after a random orthogonal similarity (QR decides the order)
+    rng = np.random.default_rng(11)
+    Qm, _ = np.linalg.qr(rng.standard_normal((7, 7)))
+    A = Qm @ M @ Qm.T
+    Q, T = pkg.schur_real(A)
+    _check_real_schur(A, Q, T)
+    assert np.count_nonzero(np.diag(T, -1)) == 2
+
+
+def test_host_real_schur_rejects_bad_input():
+    with pytest.raises(pkg.SylvError):
+        pkg.schur_real(np.full((3, 3), np.nan))
+
+
 @pytest.mark.parametrize("n,scale,seed", [(1, 0.5, 0), (2, 0.01, 1), (5, 1.0, 2), (12, 4.0, 3),
                                           (33, 0.3, 4), (40, 9.0, 5)])
 def test_host_expm_matches_scipy(n, scale, seed):
