@@ -64,7 +64,7 @@ def parse():
                     help="run each hot-path kernel family once on the workload (for ncu)")
     ap.add_argument("--workload", default="n64_N4",
                     choices=["n64_N4", "batch512", "advdiff48", "n2_N29", "n19_N7",
-                             "evolve_n64_N4"],
+                             "evolve_n64_N4", "real_n64_N4"],
                     help="n64_N4 is the benchmark line; the others measure the other "
                          "synthetic workloads (one JSON line each)")
     return ap.parse_args()
@@ -353,6 +353,75 @@ def evolve_workload(args, local: int) -> int:
     return 0
 
 
+def real_workload(args, local: int) -> int:
+    """Real A_j and B (N=4, n=64): the real-arithmetic variant (real Schur factors,
+    float64 / float32 tensors) in FP64 and mixed precision, beside the complex
+    plan solving the same problem as complex data."""
+    import torch
+    from paper_2412_15840_gb300.build import build
+    build()
+    from paper_2412_15840_gb300 import Plan, from_device, to_device
+    import oracle
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    import torch.distributed as dist
+    from paper_2412_15840_gb300.dist import max_over_ranks
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl", device_id=dev)
+    p = si.real_cube_n64_N4(seed=rank)
+    entries = p.n_tot * world
+    out = {"workload": "real_n64_N4",
+           "description": "N=4, n_k=64, real A=randn/8+3I, real unit Gaussian B, 1 RHS",
+           "entries": entries, "l2": "inputs larger than L2 (134 MB float64 tensors)"}
+    ref = None
+    if not args.no_oracle:
+        ref = oracle.solve([a.astype(np.complex128) for a in p.A],
+                           p.B.astype(np.complex128)).real
+    stream = torch.cuda.current_stream(dev)
+    legs = (("real_mixed", "mixed", True), ("real_fp64", "fp64", True),
+            ("complex_mixed", "mixed", False), ("complex_fp64", "fp64", False))
+    for name, prec, real in legs:
+        plan = Plan(A=p.A, nrhs=1, prec=prec, rtol=RTOL, max_refine=MAX_REFINE, device=local,
+                    real=real)
+        Bd = to_device(p.B if real else p.B.astype(np.complex128), device=dev)
+        X = torch.empty_like(Bd)
+        ws = torch.empty(max(plan.workspace_bytes, 256), dtype=torch.uint8, device=dev)
+        plan.set_timing(True)
+        for _ in range(args.warmup):
+            plan.solve(Bd, X=X, workspace=ws, stream=stream)
+        torch.cuda.synchronize(dev)
+        plan.timing(reset=True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            plan.solve(Bd, X=X, workspace=ws, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, device=dev)
+        tm = plan.timing(reset=True)
+        _, info = plan.solve(Bd, X=X, workspace=ws, stream=stream, info=True)
+        rec = {"ms_per_step": ms, "value": entries / (ms * 1e-3),
+               "phase_ms": {k: v / max(1, tm["solves"]) for k, v in tm["ms"].items()},
+               "refine_iters": info["refine_iters"], "status": info["status"]}
+        if ref is not None:
+            Xh = from_device(X, p.B.shape)
+            rec["rel_err_vs_oracle"] = oracle.rel_err(Xh.real if not real else Xh, ref)
+        out[name] = rec
+        del plan, X, ws, Bd
+        torch.cuda.empty_cache()
+    line = {"metric": METRIC, "unit": UNIT, "value": out["real_mixed"]["value"], "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "data": "synthetic", "dtype": "f32+f64 (real)", "config": out}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def kernels_once(local: int, small_n: bool = False) -> int:
     """One launch group of every hot-path kernel family, in this order:
     FP64 residual passes, FP32 forward passes (first mode and modes 2-4 on
@@ -405,6 +474,8 @@ def main():
         return kernels_once(local, small_n=args.workload == "n2_N29")
     if args.workload == "evolve_n64_N4":
         return evolve_workload(args, local)
+    if args.workload == "real_n64_N4":
+        return real_workload(args, local)
     if args.workload != "n64_N4":
         return other_workload(args, local)
 

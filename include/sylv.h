@@ -92,7 +92,8 @@ typedef struct {
     int32_t path;             /* bit 0: the sweep ran as the entrywise division of
                                  Remark 1 (every A_j normal, see sylv_tuning);
                                  bit 1: the residual ran on the tensor cores
-                                 (SYLV_MIXED_FP32_EMU)                                 */
+                                 (SYLV_MIXED_FP32_EMU);
+                                 bit 2: real-arithmetic plan (sylv_plan_create_real) */
     double last_corr_rel;     /* ||D_k|| / ||X_k|| of the last refinement step        */
     double est_rel_err;       /* contraction-based estimate of the final error        */
     double min_abs_den;       /* min |sum_j t_{j,i_j i_j}| over all multi-indices      */
@@ -159,6 +160,33 @@ sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t 
                              const double *const *A, const double *const *Q,
                              const double *const *T, int prec, double rtol,
                              int max_refine, int device, const sylv_tuning *tuning);
+
+/*
+ * sylv_plan_create_real -- the real-arithmetic variant for real A_j and real
+ * right-hand sides: A_j = Q_j T_j Q_j^T with Q_j orthogonal and T_j
+ * quasi-upper-triangular (real Schur form, 2 x 2 diagonal blocks for
+ * complex-conjugate eigenvalue pairs; sylv_schur_real), so the transforms of
+ * Eqs. (CUNU2U1B) and (XUNU2U1Y) run on real tensors with real Q_j (half the
+ * bytes and a quarter of the flops of the complex path).  The sweep of
+ * Eq. (yi1i2iN) keeps real C and Y in memory; inside a tile the entries coupled
+ * by 2 x 2 blocks are rotated by the blocks' unitary Schur vectors V_j to the
+ * complex triangular V_j^* T_j V_j, solved, and rotated back.
+ *   A        host array of N pointers to n_j x n_j float64 matrices (column-major).
+ *   prec     SYLV_FP64 (float64 tensors) or SYLV_MIXED_FP32 (float32 working
+ *            tensor, FP64 residual); SYLV_MIXED_FP32_EMU is not offered.
+ *   Other arguments as sylv_plan_create.
+ * A plan made here takes float64 B and X in sylv_solve / sylv_solve_batched,
+ * and its working-precision tensors (sylv_forward / sylv_sweep / sylv_back) are
+ * float64 (SYLV_FP64) or float32 (SYLV_MIXED_FP32); sylv_residual reads and
+ * writes float64.  sylv_plan_factors returns the real Q_j and T_j with zero
+ * imaginary parts.  sylv_evolve is not offered (SYLV_ERR_INVALID_ARG).
+ * SYLV_ERR_SHAPE if a sweep tile cannot hold every coupled pair: each mode with
+ * a 2 x 2 block needs a tile extent of at least 2, and a tile holds at most
+ * 8192 entries (at most 13 such modes).
+ */
+sylv_status sylv_plan_create_real(sylv_plan_t *out, int N, const int64_t *n, int64_t nrhs,
+                                  const double *const *A, int prec, double rtol, int max_refine,
+                                  int device, const sylv_tuning *tuning);
 
 sylv_status sylv_plan_destroy(sylv_plan_t plan);
 

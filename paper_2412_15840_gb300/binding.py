@@ -35,7 +35,7 @@ EXPORTED = ("sylv_plan_create", "sylv_plan_destroy", "sylv_workspace_size", "syl
             "sylv_back", "sylv_residual", "sylv_plan_factors", "sylv_plan_set_timing",
             "sylv_plan_timing", "sylv_schur", "sylv_status_string", "sylv_version",
             "sylv_sweep_static", "sylv_plan_autotune", "sylv_evolve_workspace_size",
-            "sylv_evolve", "sylv_expm", "sylv_schur_real")
+            "sylv_evolve", "sylv_expm", "sylv_schur_real", "sylv_plan_create_real")
 
 
 class SylvError(RuntimeError):
@@ -55,6 +55,7 @@ class Info(ctypes.Structure):
         d = {k: getattr(self, k) for k, _ in self._fields_}
         d["diagonal_sweep"] = bool(self.path & 1)
         d["tensor_core_residual"] = bool(self.path & 2)
+        d["real"] = bool(self.path & 4)
         return d
 
 
@@ -89,6 +90,11 @@ def _lib():
                                        ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                        ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                        ctypes.POINTER(Tuning)]
+        L.sylv_plan_create_real.restype = st
+        L.sylv_plan_create_real.argtypes = [ctypes.POINTER(vp), ctypes.c_int,
+                                            ctypes.POINTER(ctypes.c_int64), ctypes.c_int64,
+                                            ctypes.POINTER(vp), ctypes.c_int, ctypes.c_double,
+                                            ctypes.c_int, ctypes.c_int, ctypes.POINTER(Tuning)]
         L.sylv_plan_destroy.restype = st
         L.sylv_plan_destroy.argtypes = [vp]
         L.sylv_workspace_size.restype = st
@@ -215,18 +221,26 @@ def from_device(t, shape) -> np.ndarray:
 
 
 class Plan:
-    """One equation shape, its Schur factors and launch tables (sylv_plan_create)."""
+    """One equation shape, its Schur factors and launch tables (sylv_plan_create).
+
+    real=True: the real-arithmetic variant (sylv_plan_create_real) for real A
+    (float64 matrices); B and X are then float64 device tensors."""
 
     def __init__(self, A: Optional[Sequence] = None, Q: Optional[Sequence] = None,
                  T: Optional[Sequence] = None, nrhs: int = 1, prec: str = "fp64",
                  rtol: float = 1e-10, max_refine: int = 5, device: int = 0,
                  block: Optional[Sequence[int]] = None, group_max: int = 0,
                  sweep_threads: int = 0, tensor_cores: bool = True, timeout_ms: int = 0,
-                 fault_tile: int = 0, general_sweep: bool = False, sweep_ctas_per_sm: int = 0):
+                 fault_tile: int = 0, general_sweep: bool = False, sweep_ctas_per_sm: int = 0,
+                 real: bool = False):
         L = _lib()
-        if (A is None) == (Q is None or T is None):
+        self.real = bool(real)
+        if self.real and (A is None or Q is not None or T is not None):
+            raise ValueError("a real plan takes A only")
+        if (A is None) == (Q is None or T is None) and not self.real:
             raise ValueError("give A, or both Q and T")
-        mats = [_cmat(a) for a in (A if A is not None else T)]
+        mats = [np.atleast_2d(np.asarray(a, dtype=np.float64)) if self.real else _cmat(a)
+                for a in (A if A is not None else T)]
         self.shape = tuple(int(m.shape[0]) for m in mats)
         self.N = len(self.shape)
         self.nrhs = int(nrhs)
@@ -236,7 +250,7 @@ class Plan:
         keep = []
 
         def ptrs(seq):
-            arr = [_cmat(m) for m in seq]
+            arr = [np.asfortranarray(m) for m in mats] if self.real else [_cmat(m) for m in seq]
             keep.extend(arr)
             return (vp * self.N)(*[a.ctypes.data for a in arr])
 
@@ -258,10 +272,15 @@ class Plan:
             tun.general_sweep = int(bool(general_sweep))
             tun.sweep_ctas_per_sm = int(sweep_ctas_per_sm)
         h = vp()
-        s = L.sylv_plan_create(ctypes.byref(h), self.N, n, self.nrhs, pA, pQ, pT, self.prec,
-                               float(rtol), int(max_refine), int(device),
-                               ctypes.byref(tun) if tun is not None else None)
-        _check(s, "sylv_plan_create")
+        tp = ctypes.byref(tun) if tun is not None else None
+        if self.real:
+            s = L.sylv_plan_create_real(ctypes.byref(h), self.N, n, self.nrhs, pA, self.prec,
+                                        float(rtol), int(max_refine), int(device), tp)
+            _check(s, "sylv_plan_create_real")
+        else:
+            s = L.sylv_plan_create(ctypes.byref(h), self.N, n, self.nrhs, pA, pQ, pT, self.prec,
+                                   float(rtol), int(max_refine), int(device), tp)
+            _check(s, "sylv_plan_create")
         self._h = h
         sz = ctypes.c_size_t()
         _check(L.sylv_workspace_size(h, ctypes.byref(sz)), "sylv_workspace_size")
@@ -288,11 +307,26 @@ class Plan:
         ws = self.workspace() if workspace is None else workspace
         return ws.data_ptr(), ws.numel() * ws.element_size()
 
-    def solve(self, B, X=None, workspace=None, stream=None, info: bool = False):
-        """X with sum_j A_j (x)_j X = B; B, X flat complex128 device tensors."""
+    @property
+    def dtype(self):
+        """dtype of B and X: complex128, or float64 for a real plan."""
         import torch
-        if B.dtype != torch.complex128 or B.numel() != self.numel:
-            raise ValueError("B must be complex128 with prod(shape)*nrhs elements")
+        return torch.float64 if self.real else torch.complex128
+
+    @property
+    def work_dtype(self):
+        """dtype of the working-precision tensors of sylv_forward / sweep / back."""
+        import torch
+        if self.prec == SYLV_FP64:
+            return torch.float64 if self.real else torch.complex128
+        return torch.float32 if self.real else torch.complex64
+
+    def solve(self, B, X=None, workspace=None, stream=None, info: bool = False):
+        """X with sum_j A_j (x)_j X = B; B, X flat complex128 (float64 for a real
+        plan) device tensors."""
+        import torch
+        if B.dtype != self.dtype or B.numel() != self.numel:
+            raise ValueError(f"B must be {self.dtype} with prod(shape)*nrhs elements")
         if X is None:
             X = torch.empty_like(B)
         wp, wb = self._wsargs(workspace)
@@ -373,8 +407,8 @@ class Plan:
         Returns (block extents per input mode, best sweep time in ms)."""
         import torch
         if scratch is None:
-            dt = torch.complex128 if self.prec == SYLV_FP64 else torch.complex64
-            scratch = torch.empty(self.numel, dtype=dt, device=f"cuda:{self.device}")
+            scratch = torch.empty(self.numel, dtype=self.work_dtype,
+                                  device=f"cuda:{self.device}")
         wp, wb = self._wsargs(workspace)
         blk = (ctypes.c_int32 * self.N)()
         ms = ctypes.c_float()

@@ -199,8 +199,23 @@ struct sylv_plan_s {
         if (cur >= 0 && cur != device) cudaSetDevice(cur);
     }
 
+    // real-arithmetic variant (sylv_plan_create_real): real Schur factors per
+    // input mode, the pair rotations V_j (4 complex entries per index pair), the
+    // real quasi-triangular T_j and the V_j on the device; Th holds the complex
+    // triangular T~_j = V_j^* T_j V_j, Qh the real Q_j
+    bool real = false;
+    std::vector<std::vector<double>> Qr, Tr;
+    std::vector<std::vector<cd>> Vh;
+    bool has_pairs[MAXM] = {};
+    const void *Tr64[MAXM] = {}, *Tr32[MAXM] = {}, *V64[MAXM] = {}, *V32[MAXM] = {};
+
     bool fp64() const { return prec == SYLV_FP64; }
     bool emu() const { return prec == SYLV_MIXED_FP32_EMU; }
+    // element kinds and sizes of the FP64 tensors (B, X, R) and the FP32 working tensor
+    int khi() const { return real ? ELEM_R64 : ELEM_C128; }
+    int klo() const { return real ? ELEM_R32 : ELEM_C64; }
+    size_t ehi() const { return real ? 8 : 16; }
+    size_t elo() const { return real ? 4 : 8; }
 };
 
 namespace {
@@ -317,7 +332,8 @@ bool make_oz_passes(const sylv_plan_s &p, std::vector<sylv_plan_s::OzPass> &out)
 sylv_status make_groups(const sylv_plan_s &p, bool fp64, bool composition, int group_max,
                         bool allow_tc,
                         std::vector<Group> &out) {
-    const int64_t esz = fp64 ? 16 : 8;
+    const int64_t esz = (fp64 ? 16 : 8) / (p.real ? 2 : 1);
+    const bool plane = !composition && fp64 && !p.real;   // residual's re + im plane
     const int64_t Et = fp64 ? 2048 : 4096;
     const int64_t Eh = fp64 ? 8192 : 16384;
     out.clear();
@@ -327,11 +343,11 @@ sylv_status make_groups(const sylv_plan_s &p, bool fp64, bool composition, int g
         g.first = 0; g.count = 0; g.L = 1; g.P = 1; g.R = tot;
         choose_tile(1, 1, tot, Et, Eh, g.Lt, g.Rt);
         g.tilesL = 1;
-        g.smem = (size_t)(g.Lt * g.Rt) * (esz + ((!composition && fp64) ? 8 : 0));
+        g.smem = (size_t)(g.Lt * g.Rt) * (esz + (plane ? 8 : 0));
         out.push_back(g);
         return SYLV_OK;
     }
-    const bool use_tc = composition && !fp64 && allow_tc;
+    const bool use_tc = composition && !fp64 && allow_tc && !p.real;
     int j = 0;
     while (j < p.Nm) {
         Group g;
@@ -363,7 +379,7 @@ sylv_status make_groups(const sylv_plan_s &p, bool fp64, bool composition, int g
         // composition: two tiles (ping-pong); residual: the tile and its
         // re + im plane (FP64 only); otherwise one tile
         g.smem = (size_t)(E * esz * ((composition && g.count > 1) ? 2 : 1));
-        if (!composition && fp64) g.smem += (size_t)E * 8;
+        if (plane) g.smem += (size_t)E * 8;
         if (g.smem > 200 * 1024) return SYLV_ERR_SHAPE;
         out.push_back(g);
         j += g.count;
@@ -382,6 +398,11 @@ void choose_blocks(const sylv_plan_s &p, int target, const sylv_tuning *tu, int 
             manual = true;
         }
     }
+    // real variant: a mode with 2 x 2 blocks needs an even extent (or the whole
+    // mode) so that no tile splits a block
+    for (int j = 0; j < p.Nm; ++j)
+        if (p.real && p.has_pairs[j] && b[j] < p.n[j] && (b[j] & 1))
+            b[j] = (int)std::min<int64_t>(b[j] + 1, p.n[j]);
     if (manual) return;
     for (;;) {
         int best = -1;
@@ -443,6 +464,7 @@ sylv_status build_sweep(const sylv_plan_s &p, const int *b, int threads, SweepCo
     a.sig_im = p.sigma.imag();
     a.timeout_cycles = p.timeout_cycles;
     a.fault_tile = p.fault_tile;
+    a.real = p.real ? 1 : 0;
 
     // in-tile schedule: box offsets sorted by their distance from the tile end
     std::vector<int> lvl(a.Pt), cntl(a.Lin + 1, 0);
@@ -558,7 +580,7 @@ sylv_status build_sweep(const sylv_plan_s &p, const int *b, int threads, SweepCo
     // persistent grid: every SM holds as many tiles as fit, or the requested
     // number (fewer CTAs per SM shorten each tile's latency on the dependency
     // chain at the cost of tiles in flight)
-    int per = sweep_blocks_per_sm(p.fp64(), cfg.threads, cfg.smem);
+    int per = sweep_blocks_per_sm(p.fp64(), cfg.threads, cfg.smem, a.real);
     if (per < 1) per = 1;
     if (ctas_per_sm > 0 && ctas_per_sm < per) per = ctas_per_sm;
     cfg.per_sm = per;
@@ -699,7 +721,7 @@ cudaError_t run_residual(Ctx &c, const void *B, const void *X, void *R, const in
         a.first = gi == 0;
         a.flags = c.flags;
         a.done = done;
-        cudaError_t e = launch_modeprod(1, ELEM_C128, ELEM_C128, EPI_RESID, a, g.smem, c.st);
+        cudaError_t e = launch_modeprod(1, p->khi(), p->khi(), EPI_RESID, a, g.smem, c.st);
         if (e != cudaSuccess) return e;
         count(c);
     }
@@ -763,6 +785,8 @@ cudaError_t run_sweep_cfg(Ctx &c, const SweepConfig &cfg, void *Y, bool fp64) {
     for (int j = 0; j < p->Nm; ++j) {
         a.T[j] = fp64 ? p->T64[j] : p->T32[j];
         a.d[j] = p->d64[j];
+        a.Tr[j] = fp64 ? p->Tr64[j] : p->Tr32[j];
+        a.Vp[j] = p->has_pairs[j] ? (fp64 ? p->V64[j] : p->V32[j]) : nullptr;
     }
     a.den_scale = p->den_scale;
     a.inv_tab = p->inv_tab;
@@ -808,7 +832,7 @@ sylv_status fill_info(sylv_plan_s *p, DevFlags *flags, cudaStream_t st, sylv_inf
     info->status = s;
     info->refine_iters = p->fp64() ? 0 : h.iters;
     info->launches = launches;
-    info->path = (p->diag_sweep ? 1 : 0) | (p->oz ? 2 : 0);
+    info->path = (p->diag_sweep ? 1 : 0) | (p->oz ? 2 : 0) | (p->real ? 4 : 0);
     info->last_corr_rel = p->fp64() ? 0.0 : (double)h.lastcorr;
     info->est_rel_err = p->fp64() ? 0.0 : (double)h.est;
     info->min_abs_den = p->min_den;
@@ -821,6 +845,7 @@ sylv_status solve_impl(sylv_plan_s *p, const void *B, void *X, void *ws, cudaStr
     Ctx c{p, st, reinterpret_cast<DevFlags *>(ws),
           reinterpret_cast<int *>((char *)ws + p->off_cnt)};
     cudaError_t e;
+    const int KH = p->khi(), KL = p->klo();
     const bool timing = p->timing;
     cudaEvent_t t0 = nullptr;
     if (timing) { t0 = take_event(p); cudaEventRecord(t0, st); }
@@ -829,19 +854,19 @@ sylv_status solve_impl(sylv_plan_s *p, const void *B, void *X, void *ws, cudaStr
     if (p->fp64()) {
         phase_begin(c, SYLV_PH_FORWARD);
         if (p->Nm == 0) {
-            if (B != X && cudaMemcpyAsync(X, B, (size_t)(p->ntot * p->nrhs) * 16,
+            if (B != X && cudaMemcpyAsync(X, B, (size_t)(p->ntot * p->nrhs) * p->ehi(),
                                           cudaMemcpyDeviceToDevice, st) != cudaSuccess)
                 return SYLV_ERR_CUDA;
-        } else if ((e = run_groups(c, p->tgroups, true, 0, B, ELEM_C128, X, ELEM_C128, X,
-                                   ELEM_C128, EPI_STORE, nullptr)) != cudaSuccess)
+        } else if ((e = run_groups(c, p->tgroups, true, 0, B, KH, X, KH, X,
+                                   KH, EPI_STORE, nullptr)) != cudaSuccess)
             return SYLV_ERR_CUDA;
         phase_end(c);
         phase_begin(c, SYLV_PH_SWEEP);
         if ((e = run_sweep(c, X, true)) != cudaSuccess) return SYLV_ERR_CUDA;
         phase_end(c);
         phase_begin(c, SYLV_PH_BACK);
-        if (p->Nm > 0 && (e = run_groups(c, p->tgroups, true, 1, X, ELEM_C128, X, ELEM_C128, X,
-                                         ELEM_C128, EPI_STORE, nullptr)) != cudaSuccess)
+        if (p->Nm > 0 && (e = run_groups(c, p->tgroups, true, 1, X, KH, X, KH, X,
+                                         KH, EPI_STORE, nullptr)) != cudaSuccess)
             return SYLV_ERR_CUDA;
         phase_end(c);
     } else {
@@ -850,7 +875,7 @@ sylv_status solve_impl(sylv_plan_s *p, const void *B, void *X, void *ws, cudaStr
         const int *done = &c.flags->done;
         // initial low-precision solve X_0
         phase_begin(c, SYLV_PH_FORWARD);
-        if ((e = run_groups(c, p->tgroups, false, 0, B, ELEM_C128, W, ELEM_C64, W, ELEM_C64,
+        if ((e = run_groups(c, p->tgroups, false, 0, B, KH, W, KL, W, KL,
                             EPI_STORE, nullptr)) != cudaSuccess)
             return SYLV_ERR_CUDA;
         phase_end(c);
@@ -858,7 +883,7 @@ sylv_status solve_impl(sylv_plan_s *p, const void *B, void *X, void *ws, cudaStr
         if ((e = run_sweep(c, W, false)) != cudaSuccess) return SYLV_ERR_CUDA;
         phase_end(c);
         phase_begin(c, SYLV_PH_BACK);
-        if ((e = run_groups(c, p->tgroups, false, 1, W, ELEM_C64, W, ELEM_C64, X, ELEM_C128,
+        if ((e = run_groups(c, p->tgroups, false, 1, W, KL, W, KL, X, KH,
                             EPI_STORE_NORM, nullptr)) != cudaSuccess)
             return SYLV_ERR_CUDA;
         phase_end(c);
@@ -877,9 +902,9 @@ sylv_status solve_impl(sylv_plan_s *p, const void *B, void *X, void *ws, cudaStr
             }
             phase_end(c);
             phase_begin(c, SYLV_PH_FORWARD);
-            if (p->oz ? run_groups(c, p->tgroups, false, 0, W, ELEM_C64, W, ELEM_C64, W, ELEM_C64,
+            if (p->oz ? run_groups(c, p->tgroups, false, 0, W, KL, W, KL, W, KL,
                                    EPI_STORE, done) != cudaSuccess
-                      : run_groups(c, p->tgroups, false, 0, R, ELEM_C128, W, ELEM_C64, W, ELEM_C64,
+                      : run_groups(c, p->tgroups, false, 0, R, KH, W, KL, W, KL,
                                    EPI_STORE, done) != cudaSuccess)
                 return SYLV_ERR_CUDA;
             phase_end(c);
@@ -887,7 +912,7 @@ sylv_status solve_impl(sylv_plan_s *p, const void *B, void *X, void *ws, cudaStr
             if (run_sweep(c, W, false) != cudaSuccess) return SYLV_ERR_CUDA;
             phase_end(c);
             phase_begin(c, SYLV_PH_BACK);
-            if (run_groups(c, p->tgroups, false, 1, W, ELEM_C64, W, ELEM_C64, X, ELEM_C128,
+            if (run_groups(c, p->tgroups, false, 1, W, KL, W, KL, X, KH,
                            EPI_ACCUM, done) != cudaSuccess)
                 return SYLV_ERR_CUDA;
             phase_end(c);
@@ -1057,17 +1082,75 @@ sylv_status sylv_expm(int64_t n, const double *M, double *E) {
     }
 }
 
-sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t nrhs,
-                             const double *const *A, const double *const *Q,
-                             const double *const *T, int prec, double rtol, int max_refine,
-                             int device, const sylv_tuning *tuning) {
+// The 2 x 2 blocks of a real quasi-triangular T (at even offsets) rotated to
+// complex triangular form: V = [u1 u2] with u1 the unit eigenvector of the
+// block's eigenvalue lambda (positive imaginary part) and u2 = (-conj(u1[1]),
+// conj(u1[0])), so V^* B V = [lambda *; 0 conj(lambda)].  Returns V (4 complex
+// entries per index pair, identity for pairs of 1 x 1 blocks) and
+// Tt = V^* T V with its rounding-level entries below the diagonal cleared.
+static bool rotate_quasi_triangular(int64_t n, const std::vector<double> &T, std::vector<cd> &V,
+                             std::vector<cd> &Tt, bool &pairs) {
+    const int64_t np = (n + 1) / 2;
+    V.assign((size_t)(4 * np), cd(0.0));
+    pairs = false;
+    for (int64_t u = 0; u < np; ++u) {
+        cd *v = V.data() + 4 * u;
+        const int64_t k = 2 * u;
+        if (k + 1 < n && T[(size_t)(k + 1 + k * n)] != 0.0) {
+            const double a = T[(size_t)(k + k * n)], b = T[(size_t)(k + (k + 1) * n)];
+            const double c = T[(size_t)(k + 1 + k * n)], d = T[(size_t)(k + 1 + (k + 1) * n)];
+            const double p = 0.5 * (a - d), disc = p * p + b * c;
+            if (!(disc < 0.0) || b == 0.0) return false;
+            const cd lam(0.5 * (a + d), std::sqrt(-disc));
+            cd x = b, y = lam - a;
+            const double h = std::sqrt(std::norm(x) + std::norm(y));
+            x /= h;
+            y /= h;
+            v[0] = x; v[1] = y; v[2] = -std::conj(y); v[3] = std::conj(x);
+            pairs = true;
+        } else {
+            v[0] = 1.0; v[3] = 1.0;
+        }
+    }
+    // Tt = V^* T V, V block diagonal: Tt[r, c] = sum over the blocks of r and c
+    Tt.assign((size_t)(n * n), cd(0.0));
+    auto Vat = [&](int64_t r, int64_t c) -> cd {   // V[r, c], zero off the 2 x 2 blocks
+        if (r / 2 != c / 2) return cd(0.0);
+        const cd *v = V.data() + 4 * (r / 2);
+        return v[(r & 1) + 2 * (c & 1)];
+    };
+    for (int64_t c = 0; c < n; ++c)
+        for (int64_t r = 0; r < n; ++r) {
+            cd sum = 0.0;
+            for (int64_t rr = r & ~1LL; rr < std::min<int64_t>(n, (r & ~1LL) + 2); ++rr)
+                for (int64_t cc = c & ~1LL; cc < std::min<int64_t>(n, (c & ~1LL) + 2); ++cc)
+                    sum += std::conj(Vat(rr, r)) * T[(size_t)(rr + cc * n)] * Vat(cc, c);
+            Tt[(size_t)(r + c * n)] = sum;
+        }
+    double nrm = 0.0;
+    for (double t : T) nrm = std::max(nrm, std::fabs(t));
+    for (int64_t c = 0; c < n; ++c)
+        for (int64_t r = c + 1; r < n; ++r) {
+            if (std::abs(Tt[(size_t)(r + c * n)]) > 1e-12 * std::max(nrm, 1e-300)) return false;
+            Tt[(size_t)(r + c * n)] = 0.0;
+        }
+    return true;
+}
+
+static sylv_status create_plan(sylv_plan_t *out, int N, const int64_t *n, int64_t nrhs,
+                               const double *const *A, const double *const *Q,
+                               const double *const *T, const double *const *Areal, int prec,
+                               double rtol, int max_refine, int device,
+                               const sylv_tuning *tuning) {
     if (!out) return SYLV_ERR_INVALID_ARG;
     *out = nullptr;
     if (!n || N < 1 || N > 256 || nrhs < 1) return SYLV_ERR_SHAPE;
     if (prec != SYLV_FP64 && prec != SYLV_MIXED_FP32 && prec != SYLV_MIXED_FP32_EMU)
         return SYLV_ERR_INVALID_ARG;
+    const bool real = Areal != nullptr;
+    if (real && prec == SYLV_MIXED_FP32_EMU) return SYLV_ERR_INVALID_ARG;
     const bool haveA = A != nullptr, haveQT = (Q != nullptr && T != nullptr);
-    if (haveA == haveQT) return SYLV_ERR_INVALID_ARG;
+    if (real ? (haveA || haveQT) : (haveA == haveQT)) return SYLV_ERR_INVALID_ARG;
     if (prec != SYLV_FP64 && (!(rtol > 0.0) || max_refine < 1)) return SYLV_ERR_INVALID_ARG;
     sylv_plan_s *p = nullptr;
     try {
@@ -1083,6 +1166,7 @@ sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t 
     p->N_in = N;
     p->nrhs = nrhs;
     p->n_in.assign(n, n + N);
+    p->real = real;
     // shapes, strides, overflow
     int64_t tot = 1;
     for (int j = 0; j < N; ++j) {
@@ -1104,7 +1188,12 @@ sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t 
     p->Ah.resize(N);
     p->Qh.resize(N);
     p->Th.resize(N);
-    for (int j = 0; j < N; ++j) {
+    if (real) {
+        p->Qr.resize(N);
+        p->Tr.resize(N);
+        p->Vh.resize(N);
+    }
+    for (int j = 0, jm = 0; j < N; ++j) {
         const int64_t nj = n[j], nn = nj * nj;
         auto &Aj = p->Ah[j];
         auto &Qj = p->Qh[j];
@@ -1112,7 +1201,29 @@ sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t 
         Aj.assign((size_t)nn, 0.0);
         Qj.assign((size_t)nn, 0.0);
         Tj.assign((size_t)nn, 0.0);
-        if (haveA) {
+        if (real) {
+            // A_j = Q_j T_j Q_j^T (real Schur, 2 x 2 blocks at even offsets), and
+            // the complex triangular T~_j = V_j^* T_j V_j the sweep uses in a tile
+            if (!Areal[j]) return SYLV_ERR_INVALID_ARG;
+            auto &Qr = p->Qr[j];
+            auto &Tr = p->Tr[j];
+            Qr.assign((size_t)nn, 0.0);
+            Tr.assign((size_t)nn, 0.0);
+            for (int64_t k = 0; k < nn; ++k) Aj[(size_t)k] = cd(Areal[j][k], 0.0);
+            if (nj == 1) {
+                Qr[0] = 1.0;
+                Tr[0] = Areal[j][0];
+                Qj[0] = 1.0;
+                Tj[0] = Aj[0];
+            } else {
+                sylv_status s = schur_real_host(nj, Areal[j], Qr.data(), Tr.data());
+                if (s != SYLV_OK) return s;
+                bool pairs = false;
+                if (!rotate_quasi_triangular(nj, Tr, p->Vh[j], Tj, pairs)) return SYLV_ERR_SCHUR;
+                for (int64_t k = 0; k < nn; ++k) Qj[(size_t)k] = Qr[(size_t)k];
+                p->has_pairs[jm] = pairs;
+            }
+        } else if (haveA) {
             if (!A[j]) return SYLV_ERR_INVALID_ARG;
             for (int64_t k = 0; k < nn; ++k) Aj[(size_t)k] = cd(A[j][2 * k], A[j][2 * k + 1]);
             if (nj == 1) {
@@ -1149,12 +1260,13 @@ sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t 
         for (auto &z : Tj)
             if (!std::isfinite(z.real()) || !std::isfinite(z.imag())) return SYLV_ERR_INVALID_ARG;
         if (nj == 1) p->sigma += Tj[0];
+        if (nj > 1) ++jm;
     }
     // Remark 1: when every A_j is normal its Schur factor T_j is diagonal up
     // to rounding (||strict upper||_F of order n_j u ||T_j||_F); dropping that
     // part perturbs A_j at the level of the Schur step's own backward error,
     // and the sweep becomes an entrywise division
-    if (!(tuning && tuning->general_sweep) && p->Nm > 0) {
+    if (!(tuning && tuning->general_sweep) && p->Nm > 0 && !real) {
         bool diag = true;
         for (int j = 0; diag && j < p->Nm; ++j) {
             const auto &Tj = p->Th[p->orig[j]];
@@ -1205,7 +1317,7 @@ sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t 
     s = make_groups(*p, true, false, gmax, false, p->rgroups);
     if (s != SYLV_OK) return s;
     if (p->emu()) p->oz = make_oz_passes(*p, p->ozpasses);
-    if (p->fp64()) {
+    if (p->fp64() || real) {          // (no Theorem 1 passes for a real plan)
         p->egroups = p->tgroups;
     } else {
         s = make_groups(*p, true, true, gmax, false, p->egroups);
@@ -1223,6 +1335,10 @@ sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t 
         reserve((size_t)p->n[j] * 16);
         reserve(nn * 8); reserve(nn * 8); reserve(nn * 8);
         reserve(nn * 24); reserve(nn * 24);              // -A_j, exp(t A_j)
+        // real variant: T_j (FP64, FP32) and the pair rotations V_j (FP64, FP32)
+        const size_t np = (size_t)((p->n[j] + 1) / 2) * 4;
+        reserve(p->real ? nn * 8 : 0); reserve(p->real ? nn * 4 : 0);
+        reserve(p->real ? np * 16 : 0); reserve(p->real ? np * 8 : 0);
     }
     reserve(3 * sizeof(unsigned long long));
     const size_t oz_first = offs.size();
@@ -1261,7 +1377,36 @@ sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t 
         float *uh32 = (float *)(host.data() + offs[oi + 5]);
         float *u32 = (float *)(host.data() + offs[oi + 6]);
         float *t32 = (float *)(host.data() + offs[oi + 7]);
-        for (int64_t c = 0; c < nj; ++c)
+        for (int64_t c = 0; p->real && c < nj; ++c)
+            for (int64_t r = 0; r < nj; ++r) {
+                // real tensors: Q^T, Q, A as plain float64 / float32 matrices; the
+                // sweep's T~_j complex as for the complex plan
+                const size_t k = (size_t)(r + c * nj);
+                const double qt = p->Qr[jj][(size_t)(c + r * nj)], q = p->Qr[jj][k];
+                uh64[k] = qt;
+                u64[k] = q;
+                a64[k] = Aj[k].real();
+                uh32[k] = (float)qt;
+                u32[k] = (float)q;
+                t64[2 * k] = Tj[k].real(); t64[2 * k + 1] = Tj[k].imag();
+                t32[2 * k] = (float)Tj[k].real(); t32[2 * k + 1] = (float)Tj[k].imag();
+                ((double *)(host.data() + offs[oi + 10]))[k] = p->Tr[jj][k];
+                ((float *)(host.data() + offs[oi + 11]))[k] = (float)p->Tr[jj][k];
+            }
+        if (p->real) {
+            const auto &V = p->Vh[jj];
+            double *v64 = (double *)(host.data() + offs[oi + 12]);
+            float *v32 = (float *)(host.data() + offs[oi + 13]);
+            for (size_t k = 0; k < V.size(); ++k) {
+                v64[2 * k] = V[k].real(); v64[2 * k + 1] = V[k].imag();
+                v32[2 * k] = (float)V[k].real(); v32[2 * k + 1] = (float)V[k].imag();
+            }
+            p->Tr64[j] = base + offs[oi + 10];
+            p->Tr32[j] = base + offs[oi + 11];
+            p->V64[j] = base + offs[oi + 12];
+            p->V32[j] = base + offs[oi + 13];
+        }
+        for (int64_t c = 0; !p->real && c < nj; ++c)
             for (int64_t r = 0; r < nj; ++r) {
                 size_t k = (size_t)(r + c * nj);
                 cd uh = std::conj(Qj[(size_t)(c + r * nj)]);   // (U^*)[r, c]
@@ -1287,8 +1432,8 @@ sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t 
         p->U32[j] = base + offs[oi + 6];
         p->T32[j] = base + offs[oi + 7];
         double *na64 = (double *)(host.data() + offs[oi + 8]);
-        for (size_t k = 0; k < (size_t)(2 * nj * nj); ++k) na64[k] = -a64[k];
-        for (size_t k = 0; k < (size_t)(nj * nj); ++k) {
+        for (size_t k = 0; !p->real && k < (size_t)(2 * nj * nj); ++k) na64[k] = -a64[k];
+        for (size_t k = 0; !p->real && k < (size_t)(nj * nj); ++k) {
             uh64[2 * nj * nj + k] = uh64[2 * k] + uh64[2 * k + 1];
             u64[2 * nj * nj + k] = u64[2 * k] + u64[2 * k + 1];
             a64[2 * nj * nj + k] = a64[2 * k] + a64[2 * k + 1];
@@ -1296,7 +1441,7 @@ sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t 
         }
         p->nA64[j] = base + offs[oi + 8];
         p->E64[j] = base + offs[oi + 9];
-        oi += 10;
+        oi += 14;
     }
     unsigned long long *dm = (unsigned long long *)(base + offs[oi]);
     unsigned long long init3[3] = {~0ull, 0ull, 0ull};
@@ -1445,13 +1590,29 @@ sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t 
     w = align256(w + (size_t)p->cnt_capacity * 4);
     if (!p->fp64()) {
         p->off_W = w;
-        w = align256(w + (size_t)(p->ntot * p->nrhs) * 8);
+        w = align256(w + (size_t)(p->ntot * p->nrhs) * p->elo());
         p->off_R = w;
-        w = align256(w + (size_t)(p->ntot * p->nrhs) * 16);
+        w = align256(w + (size_t)(p->ntot * p->nrhs) * p->ehi());
     }
     p->ws_bytes = w;
     *out = guard.release();
     return SYLV_OK;
+}
+
+sylv_status sylv_plan_create(sylv_plan_t *out, int N, const int64_t *n, int64_t nrhs,
+                             const double *const *A, const double *const *Q,
+                             const double *const *T, int prec, double rtol, int max_refine,
+                             int device, const sylv_tuning *tuning) {
+    return create_plan(out, N, n, nrhs, A, Q, T, nullptr, prec, rtol, max_refine, device, tuning);
+}
+
+sylv_status sylv_plan_create_real(sylv_plan_t *out, int N, const int64_t *n, int64_t nrhs,
+                                  const double *const *A, int prec, double rtol, int max_refine,
+                                  int device, const sylv_tuning *tuning) {
+    if (out) *out = nullptr;
+    if (!A) return SYLV_ERR_INVALID_ARG;
+    return create_plan(out, N, n, nrhs, nullptr, nullptr, nullptr, A, prec, rtol, max_refine,
+                       device, tuning);
 }
 
 sylv_status sylv_plan_destroy(sylv_plan_t plan) {
@@ -1551,7 +1712,7 @@ sylv_status sylv_plan_autotune(sylv_plan_t p, void *Tdev, void *ws, size_t ws_by
     DeviceGuard dg(p->device);
     if (!dg.ok) return SYLV_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)stream;
-    const size_t esz = p->fp64() ? 16 : 8;
+    const size_t esz = p->fp64() ? p->ehi() : p->elo();
     batch_forget(p);
     if (cudaMemsetAsync(Tdev, 0, (size_t)(p->ntot * p->nrhs) * esz, st) != cudaSuccess)
         return SYLV_ERR_CUDA;
@@ -1622,14 +1783,14 @@ sylv_status sylv_plan_autotune(sylv_plan_t p, void *Tdev, void *ws, size_t ws_by
 // ------------------------------------------------------------ Theorem 1 --
 
 sylv_status sylv_evolve_workspace_size(sylv_plan_t p, size_t *bytes) {
-    if (!p || !bytes) return SYLV_ERR_INVALID_ARG;
+    if (!p || !bytes || p->real) return SYLV_ERR_INVALID_ARG;
     *bytes = align256(p->ws_bytes) + align256((size_t)(p->ntot * p->nrhs) * 16);
     return SYLV_OK;
 }
 
 sylv_status sylv_evolve(sylv_plan_t p, double t, const void *B, const void *X0, void *X,
                         void *ws, size_t ws_bytes, void *stream, sylv_info *info) {
-    if (!p || !B || !X0 || !X || !std::isfinite(t)) return SYLV_ERR_INVALID_ARG;
+    if (!p || !B || !X0 || !X || !std::isfinite(t) || p->real) return SYLV_ERR_INVALID_ARG;
     if ((((uintptr_t)B) | ((uintptr_t)X0) | ((uintptr_t)X)) & 15) return SYLV_ERR_INVALID_ARG;
     size_t need = 0;
     sylv_evolve_workspace_size(p, &need);
@@ -1757,7 +1918,7 @@ sylv_status sylv_forward(sylv_plan_t p, void *Tdev, void *ws, size_t ws_bytes, v
     if (!dg.ok) return SYLV_ERR_CUDA;
     Ctx c{p, (cudaStream_t)stream, reinterpret_cast<DevFlags *>(ws), nullptr};
     if (p->Nm == 0) return SYLV_OK;
-    int k = p->fp64() ? ELEM_C128 : ELEM_C64;
+    int k = p->fp64() ? p->khi() : p->klo();
     if (run_groups(c, p->tgroups, p->fp64(), 0, Tdev, k, Tdev, k, Tdev, k, EPI_STORE, nullptr) !=
         cudaSuccess)
         return SYLV_ERR_CUDA;
@@ -1772,7 +1933,7 @@ sylv_status sylv_back(sylv_plan_t p, void *Tdev, void *ws, size_t ws_bytes, void
     if (!dg.ok) return SYLV_ERR_CUDA;
     Ctx c{p, (cudaStream_t)stream, reinterpret_cast<DevFlags *>(ws), nullptr};
     if (p->Nm == 0) return SYLV_OK;
-    int k = p->fp64() ? ELEM_C128 : ELEM_C64;
+    int k = p->fp64() ? p->khi() : p->klo();
     if (run_groups(c, p->tgroups, p->fp64(), 1, Tdev, k, Tdev, k, Tdev, k, EPI_STORE, nullptr) !=
         cudaSuccess)
         return SYLV_ERR_CUDA;
@@ -1804,6 +1965,15 @@ sylv_status sylv_residual(sylv_plan_t p, const void *B, const void *X, void *R, 
 
 sylv_status sylv_plan_factors(sylv_plan_t p, int j, double *Qo, double *To) {
     if (!p || !Qo || !To || j < 0 || j >= p->N_in) return SYLV_ERR_INVALID_ARG;
+    if (p->real) {            // real Q_j and quasi-triangular T_j, zero imaginary parts
+        const auto &Q = p->Qr[(size_t)j];
+        const auto &T = p->Tr[(size_t)j];
+        for (size_t k = 0; k < Q.size(); ++k) {
+            Qo[2 * k] = Q[k]; Qo[2 * k + 1] = 0.0;
+            To[2 * k] = T[k]; To[2 * k + 1] = 0.0;
+        }
+        return SYLV_OK;
+    }
     const auto &Q = p->Qh[(size_t)j];
     const auto &T = p->Th[(size_t)j];
     for (size_t k = 0; k < Q.size(); ++k) {

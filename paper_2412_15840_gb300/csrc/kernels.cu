@@ -444,6 +444,8 @@ static cudaError_t set_smem_attr() {
 
 cudaError_t launch_modeprod(int fp64, int in_kind, int out_kind, int epi, const MPArgs &a,
                             size_t smem, cudaStream_t st) {
+    if (in_kind == ELEM_R32 || in_kind == ELEM_R64)
+        return launch_modeprod_real(fp64, in_kind, out_kind, epi, a, smem, st);
     int64_t tiles = a.tilesL * ((a.R + a.Rt - 1) / a.Rt);
     if (tiles <= 0) return cudaSuccess;
     if (tiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
@@ -620,6 +622,7 @@ cudaError_t kernels_init(int) {
         return e;
     if ((e = modeprod_tc_init_attrs()) != cudaSuccess) return e;
     if ((e = resid_oz_init_attrs()) != cudaSuccess) return e;
+    if ((e = modeprod_real_init_attrs()) != cudaSuccess) return e;
     return sweep_init_attrs();
 }
 

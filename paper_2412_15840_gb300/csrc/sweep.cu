@@ -29,6 +29,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <type_traits>
 
 #include "cplx.cuh"
 #include "sylv_internal.h"
@@ -68,15 +69,89 @@ __device__ __forceinline__ float2 apply_inv(float2 n, float4 v) {
     return make_float2(fmaf(n.x, v.x, tx), fmaf(n.x, v.y, ty));
 }
 
-template <typename real>
+// Real-arithmetic variant (RL): C, Y and the strips are real (YT = real), the
+// tile itself is complex.  After the strips are subtracted, the tile's
+// right-hand side is rotated into the basis of the complex triangular
+// T~_j = V_j^* T_j V_j along every in-tile mode with 2 x 2 blocks (V_j unitary,
+// block diagonal, one 2 x 2 factor per pair of indices), the in-tile wavefront
+// runs with T~_j, and the result is rotated back by V_j; its real part is Y.
+// This is exact for the quasi-triangular T_j because tiles never split a 2 x 2
+// block (its indices 2u, 2u + 1 and even tile offsets).
+__device__ __forceinline__ void cmsub(float &acc, float t, float y) { acc = fmaf(-t, y, acc); }
+__device__ __forceinline__ void cmsub(double &acc, double t, double y) { acc = fma(-t, y, acc); }
+__device__ __forceinline__ void shfl_add(float2 &v, int o) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+}
+__device__ __forceinline__ void shfl_add(double2 &v, int o) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+}
+__device__ __forceinline__ void shfl_add(float &v, int o) { v += __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ void shfl_add(double &v, int o) { v += __shfl_xor_sync(0xffffffffu, v, o); }
+template <typename C2> __device__ __forceinline__ void add_to(C2 &v, C2 a) { v.x += a.x; v.y += a.y; }
+__device__ __forceinline__ void add_to(float2 &v, float a) { v.x += a; }
+__device__ __forceinline__ void add_to(double2 &v, double a) { v.x += a; }
+template <typename C2> __device__ __forceinline__ C2 as_tile(C2 v) { return v; }
+__device__ __forceinline__ float2 as_tile(float v) { return make_float2(v, 0.f); }
+__device__ __forceinline__ double2 as_tile(double v) { return make_double2(v, 0.0); }
+template <typename YT, typename C2> __device__ __forceinline__ YT from_tile(C2 v) {
+    if constexpr (std::is_same<YT, C2>::value) return v;
+    else return v.x;
+}
+
+// [x0; x1] <- V^* [x0; x1] (adj) or V [x0; x1] on the pairs (t, t + 1), t even,
+// of every in-tile mode that has 2 x 2 blocks; V is column-major (v00, v10,
+// v01, v11).  Entries outside a partial tile hold zeros and stay zero.
+template <typename C2>
+__device__ __forceinline__ void rotate_pairs(const SweepArgs &a, C2 *tile_s, const int *be,
+                                             const int64_t *o, bool adj) {
+    for (int q = 0; q < a.nin; ++q) {
+        const int j = a.inmode[q];
+        if (!a.Vp[j]) continue;
+        const C2 *V = reinterpret_cast<const C2 *>(a.Vp[j]);
+        const int bq = a.b[j], sq = a.BS[q], half = (bq + 1) / 2;
+        const int npair = a.Pt / bq * half;
+        const int64_t u0 = o[j] / 2;
+        for (int idx = threadIdx.x; idx < npair; idx += blockDim.x) {
+            const int lo = idx % sq;
+            const int rest = idx / sq;
+            const int u = rest % half;
+            const int hi = rest / half;
+            if (2 * u + 1 >= be[j]) continue;
+            const int e0 = lo + sq * (2 * u) + hi * sq * bq;
+            const C2 x0 = tile_s[e0], x1 = tile_s[e0 + sq];
+            const C2 *v = V + 4 * (u0 + u);
+            const C2 v00 = v[0], v10 = v[1], v01 = v[2], v11 = v[3];
+            C2 y0, y1;
+            if (adj) {      // conj(v00) x0 + conj(v10) x1, conj(v01) x0 + conj(v11) x1
+                y0.x = v00.x * x0.x + v00.y * x0.y + v10.x * x1.x + v10.y * x1.y;
+                y0.y = v00.x * x0.y - v00.y * x0.x + v10.x * x1.y - v10.y * x1.x;
+                y1.x = v01.x * x0.x + v01.y * x0.y + v11.x * x1.x + v11.y * x1.y;
+                y1.y = v01.x * x0.y - v01.y * x0.x + v11.x * x1.y - v11.y * x1.x;
+            } else {        // v00 x0 + v01 x1, v10 x0 + v11 x1
+                y0.x = v00.x * x0.x - v00.y * x0.y + v01.x * x1.x - v01.y * x1.y;
+                y0.y = v00.x * x0.y + v00.y * x0.x + v01.x * x1.y + v01.y * x1.x;
+                y1.x = v10.x * x0.x - v10.y * x0.y + v11.x * x1.x - v11.y * x1.y;
+                y1.y = v10.x * x0.y + v10.y * x0.x + v11.x * x1.y + v11.y * x1.x;
+            }
+            tile_s[e0] = y0;
+            tile_s[e0 + sq] = y1;
+        }
+        __syncthreads();
+    }
+}
+
+template <typename real, bool RL>
 __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const __grid_constant__ SweepArgs a) {
     using C2 = typename C2T<real>::type;
+    using YT = typename std::conditional<RL, real, C2>::type;   // element of C and Y
     using Inv = typename InvT<real>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Inv *inv_s = reinterpret_cast<Inv *>(smem_raw);
     C2 *tile_s = reinterpret_cast<C2 *>(inv_s + a.Pt);
-    C2 *Ts = tile_s + a.Pt;                       // SW_KCH x bmax block of T_j
-    C2 *Td = Ts + SW_KCH * a.bmax;                // diagonal blocks of the in-tile modes
+    YT *Ts = reinterpret_cast<YT *>(tile_s + a.Pt);   // SW_KCH x bmax block of T_j
+    C2 *Td = tile_s + a.Pt + SW_KCH * a.bmax;         // diagonal blocks of the in-tile modes
     // packed in-tile coordinates and the level schedule of the full box, copied
     // once per CTA (every tile uses the same tables)
     unsigned long long *coord_s = reinterpret_cast<unsigned long long *>(Td + a.tdsize);
@@ -89,11 +164,11 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
     // strips, applied entry by entry in stage 1a without extra barriers
     __shared__ int s_npair, s_inlist[MAXM], s_pbase[MAXM];
     __shared__ int64_t s_pstride[SW_OUT];
-    __shared__ C2 s_pt[SW_OUT];
+    __shared__ YT s_pt[SW_OUT];
     __shared__ double s_den0x, s_den0y;
 
     if (*(volatile const int *)&a.flags->done) return;
-    C2 *Y = reinterpret_cast<C2 *>(a.Y);
+    YT *Y = reinterpret_cast<YT *>(a.Y);
     const int Nm = a.Nm, nin = a.nin, nt = blockDim.x;
     if (a.fast) {
         for (int e = threadIdx.x; e < a.Pt; e += nt) {
@@ -192,7 +267,7 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
                 if (!s_inlist[j]) continue;
                 const int K = s_cnt[j], base = s_pbase[j];
                 const int64_t nj = a.n[j], oj = s_o[j];
-                const C2 *Tj = reinterpret_cast<const C2 *>(a.T[j]);
+                const YT *Tj = reinterpret_cast<const YT *>(RL ? a.Tr[j] : a.T[j]);
                 for (int k = threadIdx.x; k < K; k += nt) {
                     s_pstride[base + k] = (int64_t)(1 + k) * a.S[j];
                     s_pt[base + k] = __ldg(Tj + oj + (oj + 1 + k) * nj);
@@ -237,9 +312,9 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
                 tile_s[e] = czero<C2>();
                 continue;
             }
-            C2 cv = __ldcg(Y + g);
+            YT cv = __ldcg(Y + g);
             for (int p0 = 0; p0 < npair; p0 += 4) {        // 4 strip loads in flight
-                C2 y[4];
+                YT y[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
                     if (p0 + u < npair) y[u] = __ldcg(Y + g + s_pstride[p0 + u]);
@@ -247,7 +322,7 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
                 for (int u = 0; u < 4; ++u)
                     if (p0 + u < npair) cmsub(cv, s_pt[p0 + u], y[u]);
             }
-            tile_s[e] = cv;
+            tile_s[e] = as_tile(cv);
             if (a.inv_tab)       // reciprocals formed once per plan (k_inv_table)
                 inv_s[e] = __ldg(reinterpret_cast<const Inv *>(a.inv_tab) + (g - s_rhs0));
             else
@@ -278,7 +353,7 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
             const int F = a.Pt / bj;                // fibers of the box along mode j
             const int64_t nj = a.n[j], Sj = a.S[j], oj = s_o[j];
             const int64_t kend = oj + bej;
-            const C2 *Tj = reinterpret_cast<const C2 *>(a.T[j]);
+            const YT *Tj = reinterpret_cast<const YT *>(RL ? a.Tr[j] : a.T[j]);
             for (int k0 = 0; k0 < K; k0 += SW_KCH) {
                 const int kk = min(SW_KCH, K - k0);
                 for (int idx = threadIdx.x; idx < bej * kk; idx += nt) {
@@ -318,20 +393,20 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
                         }
                     }
                     const int c0 = min(kk, h * per), c1 = ok ? min(kk, c0 + per) : c0;
-                    const C2 *ybase = Y + g0 + (kend + k0 - oj + c0) * Sj;
+                    const YT *ybase = Y + g0 + (kend + k0 - oj + c0) * Sj;
                     const int ncol = c1 - c0;
                     for (int rg = 0; rg < bej; rg += SW_RG) {
-                        C2 acc[SW_RG];
+                        YT acc[SW_RG];
 #pragma unroll
-                        for (int r = 0; r < SW_RG; ++r) acc[r] = czero<C2>();
-                        const C2 *yp = ybase;
-                        const C2 *tc = Ts + rg + c0 * bj;
+                        for (int r = 0; r < SW_RG; ++r) acc[r] = YT{};
+                        const YT *yp = ybase;
+                        const YT *tc = Ts + rg + c0 * bj;
                         int c = 0;
                         // FP32: 8 strip loads in flight per thread (the loads are
                         // latency-bound); FP64 keeps 4 (register budget)
                         constexpr int UNR = sizeof(real) == 4 ? 8 : 4;
                         for (; UNR == 8 && c + 8 <= ncol; c += 8) {
-                            C2 y[8];
+                            YT y[8];
 #pragma unroll
                             for (int u = 0; u < 8; ++u) y[u] = __ldcg(yp + u * Sj);
                             yp += 8 * Sj;
@@ -345,8 +420,8 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
                             tc += 8 * bj;
                         }
                         for (; c + 4 <= ncol; c += 4) {
-                            const C2 y0 = __ldcg(yp), y1 = __ldcg(yp + Sj);
-                            const C2 y2 = __ldcg(yp + 2 * Sj), y3 = __ldcg(yp + 3 * Sj);
+                            const YT y0 = __ldcg(yp), y1 = __ldcg(yp + Sj);
+                            const YT y2 = __ldcg(yp + 2 * Sj), y3 = __ldcg(yp + 3 * Sj);
                             yp += 4 * Sj;
 #pragma unroll
                             for (int r = 0; r < SW_RG; ++r) {
@@ -360,7 +435,7 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
                             tc += 4 * bj;
                         }
                         for (; c < ncol; ++c) {
-                            const C2 y = __ldcg(yp);
+                            const YT y = __ldcg(yp);
                             yp += Sj;
 #pragma unroll
                             for (int r = 0; r < SW_RG; ++r)
@@ -369,19 +444,12 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
                         }
                         for (int o = 1; o < H; o <<= 1) {
 #pragma unroll
-                            for (int r = 0; r < SW_RG; ++r) {
-                                acc[r].x += __shfl_xor_sync(0xffffffffu, acc[r].x, o);
-                                acc[r].y += __shfl_xor_sync(0xffffffffu, acc[r].y, o);
-                            }
+                            for (int r = 0; r < SW_RG; ++r) shfl_add(acc[r], o);
                         }
                         if (ok && h == 0) {
 #pragma unroll
                             for (int r = 0; r < SW_RG; ++r) {
-                                if (rg + r < bej) {
-                                    C2 &v = tile_s[e0 + (rg + r) * bs];
-                                    v.x += acc[r].x;
-                                    v.y += acc[r].y;
-                                }
+                                if (rg + r < bej) add_to(tile_s[e0 + (rg + r) * bs], acc[r]);
                             }
                         }
                     }
@@ -389,6 +457,8 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
                 __syncthreads();
             }
         }
+
+        if constexpr (RL) rotate_pairs(a, tile_s, s_be, s_o, true);
 
         // stage 2: in-tile wavefront over index sums measured from the tile's end.
         // SW_SUB consecutive lanes share an entry: lane `sub` sums the in-tile
@@ -456,6 +526,8 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
             __syncthreads();
         }
 
+        if constexpr (RL) rotate_pairs(a, tile_s, s_be, s_o, false);
+
         // stage 3: store Y and release the tiles that wait on this one
         for (int e = threadIdx.x; e < a.Pt; e += nt) {
             int64_t g = gbase;
@@ -478,7 +550,7 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
                     g += (int64_t)t * a.S[j];
                 }
             }
-            if (ok) __stcg(Y + g, tile_s[e]);
+            if (ok) __stcg(Y + g, from_tile<YT>(tile_s[e]));
         }
         __threadfence();
         __syncthreads();
@@ -541,10 +613,16 @@ cudaError_t launch_inv_table(int fp64, const SweepArgs &a, void *tab, int num_sm
 cudaError_t launch_sweep(int fp64, const SweepArgs &a, int grid, int threads, size_t smem,
                          cudaStream_t st) {
     if (a.ntiles <= 0) return cudaSuccess;
-    if (fp64)
-        k_sweep<double><<<grid, threads, smem, st>>>(a);
-    else
-        k_sweep<float><<<grid, threads, smem, st>>>(a);
+    if (a.real) {
+        if (fp64)
+            k_sweep<double, true><<<grid, threads, smem, st>>>(a);
+        else
+            k_sweep<float, true><<<grid, threads, smem, st>>>(a);
+    } else if (fp64) {
+        k_sweep<double, false><<<grid, threads, smem, st>>>(a);
+    } else {
+        k_sweep<float, false><<<grid, threads, smem, st>>>(a);
+    }
     return cudaGetLastError();
 }
 
@@ -632,21 +710,34 @@ cudaError_t launch_sweep_diag(int fp64, const DiagArgs &a, int num_sms, cudaStre
     return cudaGetLastError();
 }
 
-int sweep_blocks_per_sm(int fp64, int threads, size_t smem) {
+int sweep_blocks_per_sm(int fp64, int threads, size_t smem, int real) {
     int nb = 0;
-    cudaError_t e = fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep<double>,
-                                                                         threads, smem)
-                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep<float>,
-                                                                         threads, smem);
+    cudaError_t e;
+    if (real)
+        e = fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep<double, true>,
+                                                                 threads, smem)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep<float, true>,
+                                                                 threads, smem);
+    else
+        e = fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep<double, false>,
+                                                                 threads, smem)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep<float, false>,
+                                                                 threads, smem);
     return e == cudaSuccess ? nb : 0;
 }
 
 cudaError_t sweep_init_attrs() {
-    cudaError_t e = cudaFuncSetAttribute(k_sweep<double>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_sweep<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                200 * 1024);
+    const int big = 200 * 1024;
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_sweep<double, false>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_sweep<float, false>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_sweep<double, true>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess)
+        return e;
+    return cudaFuncSetAttribute(k_sweep<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                big);
 }
 
 }  // namespace sylv

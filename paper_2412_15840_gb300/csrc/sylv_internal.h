@@ -44,7 +44,9 @@ static_assert(sizeof(DevFlags) == 64, "DevFlags layout");
 enum { ERRBIT_TIMEOUT = 1, ERRBIT_NOTCONV = 2, ERRBIT_NAN = 4 };
 
 enum Epi { EPI_STORE = 0, EPI_RESID = 1, EPI_ACCUM = 2, EPI_STORE_NORM = 3, EPI_SUB = 4 };
-enum ElemKind { ELEM_C64 = 0, ELEM_C128 = 1 };
+// element types of a tensor: complex64 / complex128, or float32 / float64 for
+// the real-arithmetic variant
+enum ElemKind { ELEM_C64 = 0, ELEM_C128 = 1, ELEM_R32 = 2, ELEM_R64 = 3 };
 
 // One transform pass over the view (L, P, R) of a tensor, where P is the
 // product of the sizes of `G` adjacent modes; tiles are Lt x P x Rt.
@@ -102,6 +104,15 @@ struct SweepArgs {
     long long timeout_cycles;
     int fault_tile;           // test hook: this tile never releases its predecessors (-1: none)
     const void *inv_tab;      // per multi-index reciprocals in the sweep's format, or null
+    // real-arithmetic variant (real = 1): C and Y are real; T holds the complex
+    // triangular T~_j = V_j^* T_j V_j (in-tile blocks and diagonal), Tr the real
+    // quasi-triangular T_j (strips of solved tiles), Vp the unitary 2 x 2 Schur
+    // vectors V of the diagonal blocks, 4 complex entries (column-major) per
+    // pair of indices (2u, 2u + 1), identity where both are 1 x 1 blocks; null
+    // for a mode without 2 x 2 blocks
+    int real;
+    const void *Tr[MAXM];
+    const void *Vp[MAXM];
 };
 
 // Sweep of a plan whose T_j are all diagonal (every A_j normal, Remark 1):
@@ -198,7 +209,11 @@ cudaError_t launch_den_minmax(int Nm, const int64_t *n, const double *const *d, 
                               cudaStream_t st);
 cudaError_t kernels_init(int device);
 cudaError_t sweep_init_attrs();
-int sweep_blocks_per_sm(int fp64, int threads, size_t smem);
+int sweep_blocks_per_sm(int fp64, int threads, size_t smem, int real = 0);
+// real-arithmetic mode products (float32 / float64 tensors, real matrices)
+cudaError_t launch_modeprod_real(int fp64, int in_kind, int out_kind, int epi, const MPArgs &a,
+                                 size_t smem, cudaStream_t st);
+cudaError_t modeprod_real_init_attrs();
 #endif
 
 }  // namespace sylv
