@@ -426,9 +426,11 @@ def kernels_once(local: int, small_n: bool = False) -> int:
     """One launch group of every hot-path kernel family, in this order:
     FP64 residual passes, FP32 forward passes (first mode and modes 2-4 on
     the tensor cores), FP32 sweep, FP32 back passes, FP64 forward passes,
-    FP64 sweep, then one solve with the tensor-core residual (a short, fixed
-    launch sequence for ncu captures).  With --workload n2_N29: the same
-    sequence (without the last solve) on the n = 2 operators at N = 25."""
+    FP64 sweep, then one solve with the tensor-core residual, then one mixed
+    solve of the real-arithmetic variant on real operators of the same shape
+    (a short, fixed launch sequence for ncu captures).  With --workload n2_N29:
+    the same sequence (without the last two solves) on the n = 2 operators at
+    N = 25."""
     import torch
     from paper_2412_15840_gb300.build import build
     build()
@@ -458,6 +460,12 @@ def kernels_once(local: int, small_n: bool = False) -> int:
         # one solve with the tensor-core residual (k_resid_oz passes)
         e = Plan(A=p.A, nrhs=1, prec="mixed_emu", device=local)
         e.solve(B, torch.empty_like(B))
+        # one mixed solve of the real-arithmetic variant (k_modeprod_r, the
+        # tensor-core passes on the complex view, k_sweep<float, true>)
+        q = si.real_cube_n64_N4()
+        r = Plan(A=q.A, nrhs=1, prec="mixed", real=True, device=local)
+        Br = to_device(q.B, device=dev)
+        r.solve(Br, torch.empty_like(Br))
     torch.cuda.synchronize(dev)
     print("kernels-once ok")
     return 0

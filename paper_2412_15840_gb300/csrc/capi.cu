@@ -34,6 +34,9 @@ struct Group {
     int Kp = 0, Np = 0, lboA = 0, sboA = 0, sboB = 0, abytes = 0, bimg_bytes = 0;
     int tmem_cols = 0, nbuf = 1;
     const unsigned char *img[2] = {nullptr, nullptr};
+    // real plan: the pass runs on the complex view of the real tensor (pairs of
+    // entries adjacent in memory as one complex entry; L counts those pairs)
+    int cview = 0;
 };
 
 // A mode after the first runs on the tensor cores when its fibres are at least
@@ -347,17 +350,31 @@ sylv_status make_groups(const sylv_plan_s &p, bool fp64, bool composition, int g
         out.push_back(g);
         return SYLV_OK;
     }
-    const bool use_tc = composition && !fp64 && allow_tc && !p.real;
+    const bool use_tc = composition && !fp64 && allow_tc;
+    // A real plan's mode with an even stride runs on the tensor cores over the
+    // complex view of the float32 tensor: two entries adjacent in memory differ
+    // in an earlier mode's index, so a later mode's product treats them alike,
+    // and the real Q_j (a complex matrix with zero imaginary part) maps the pair
+    // (x_2a, x_2a+1) as one complex entry x_2a + i x_2a+1.
+    auto tc_ok = [&](int jj) {
+        if (!use_tc) return false;
+        if (!p.real) return tc_mode_ok(p.S[jj], p.n[jj]);
+        return p.S[jj] % 2 == 0 && tc_mode_ok(p.S[jj] / 2, p.n[jj]);
+    };
     int j = 0;
     while (j < p.Nm) {
         Group g;
         g.first = j;
         g.L = p.S[j];
-        const bool m1 = use_tc && j == 0 && tc_mode1_ok(p.n[0], tot / p.n[0], p.Nm);
-        if (m1 || (use_tc && tc_mode_ok(g.L, p.n[j]))) {
+        const bool m1 = use_tc && !p.real && j == 0 && tc_mode1_ok(p.n[0], tot / p.n[0], p.Nm);
+        if (m1 || tc_ok(j)) {
             g.count = 1;
             g.P = p.n[j];
             g.R = tot / (g.L * g.P);
+            if (p.real) {
+                g.cview = 1;
+                g.L = p.S[j] / 2;
+            }
             g.tilesL = m1 ? 1 : (g.L + 63) / 64;
             tc_geometry(g, (int)p.n[j], m1);
             out.push_back(g);
@@ -369,8 +386,7 @@ sylv_status make_groups(const sylv_plan_s &p, bool fp64, bool composition, int g
         g.P = p.n[j];
         g.count = 1;
         while (j + g.count < p.Nm && g.count < MAXG && g.P * p.n[j + g.count] <= Pcap &&
-               p.S[j + g.count] == g.L * g.P &&
-               !(use_tc && tc_mode_ok(p.S[j + g.count], p.n[j + g.count])))
+               p.S[j + g.count] == g.L * g.P && !tc_ok(j + g.count))
             g.P *= p.n[j + g.count], g.count++;
         g.R = tot / (g.L * g.P);
         if (!choose_tile(g.L, g.P, g.R, Et, Eh, g.Lt, g.Rt)) return SYLV_ERR_SHAPE;
@@ -664,6 +680,11 @@ cudaError_t run_groups(Ctx &c, const std::vector<Group> &gs, bool fp64, int whic
         int epi = last ? last_epi : EPI_STORE;
         if (g.count == 0 && a.in == a.out && epi == EPI_STORE) continue;   // identity
         if (g.tc) {
+            if (g.cview) {     // float32 / float64 tensors as complex64 / complex128 pairs
+                if (in_kind == ELEM_R32) in_kind = ELEM_C64;
+                if (out_kind == ELEM_R32) out_kind = ELEM_C64;
+                if (out_kind == ELEM_R64) out_kind = ELEM_C128;
+            }
             if (in_kind != ELEM_C64 && !(g.mode1 && in_kind == ELEM_C128))
                 return cudaErrorInvalidValue;
             if (mats) return cudaErrorInvalidValue;   // B images hold U^* and U only

@@ -183,39 +183,11 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
             const int t = atomicAdd(&a.flags->ticket, 1);
             s_ticket = t;
             s_abort = 0;
-            if (t < a.ntiles) {
-                const int tile = a.order[t];
-                s_tile = tile;
-                volatile int *c = a.cnt + tile;
-                volatile int *err = &a.flags->err;
-                const long long t0 = clock64();
-                while (*c > 0) {
-                    if (*err) { s_abort = 1; break; }
-                    if (clock64() - t0 > a.timeout_cycles) {
-                        atomicOr(&a.flags->err, ERRBIT_TIMEOUT);
-                        s_abort = 1;
-                        break;
-                    }
-                    __nanosleep(100);
-                }
-                __threadfence();
-            }
+            if (t < a.ntiles) s_tile = a.order[t];
         }
         __syncthreads();
         if (s_ticket >= a.ntiles) break;
         const int tile = s_tile;
-        if (s_abort) {
-            // drain: mark this tile finished so that nothing waits on it
-            if (threadIdx.x == 0) {
-                const int64_t rem = tile % a.ntiles1;
-                for (int j = 0; j < Nm; ++j) {
-                    const int Ij = (int)((rem / a.TS[j]) % a.Bc[j]);
-                    if (Ij > 0) atomicSub(a.cnt + tile - a.TS[j], 1);
-                }
-            }
-            __syncthreads();
-            continue;
-        }
 
         // tile geometry
         if (threadIdx.x == 0) {
@@ -276,7 +248,9 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
             __syncthreads();
         }
 
-        // stage 1a: C and the FP64 reciprocals of the diagonal sums
+        // stage 1a: C, the FP64 reciprocals of the diagonal sums and the diagonal
+        // T blocks -- this tile's own data, loaded before the wait for its
+        // successors so that the loads overlap it
         for (int e = threadIdx.x; e < a.Pt; e += nt) {
             int64_t g = gbase;
             bool ok = true;
@@ -312,17 +286,7 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
                 tile_s[e] = czero<C2>();
                 continue;
             }
-            YT cv = __ldcg(Y + g);
-            for (int p0 = 0; p0 < npair; p0 += 4) {        // 4 strip loads in flight
-                YT y[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (p0 + u < npair) y[u] = __ldcg(Y + g + s_pstride[p0 + u]);
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (p0 + u < npair) cmsub(cv, s_pt[p0 + u], y[u]);
-            }
-            tile_s[e] = as_tile(cv);
+            tile_s[e] = as_tile(__ldcg(Y + g));
             if (a.inv_tab)       // reciprocals formed once per plan (k_inv_table)
                 inv_s[e] = __ldg(reinterpret_cast<const Inv *>(a.inv_tab) + (g - s_rhs0));
             else
@@ -340,7 +304,75 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
                 dst[r + c * bj] = __ldg(Tj + (oj + r) + (oj + c) * nj);
             }
         }
+
+        // wait (bounded) until every immediate successor tile is solved
+        if (threadIdx.x == 0) {
+            volatile int *c = a.cnt + tile;
+            volatile int *err = &a.flags->err;
+            const long long t0 = clock64();
+            while (*c > 0) {
+                if (*err) { s_abort = 1; break; }
+                if (clock64() - t0 > a.timeout_cycles) {
+                    atomicOr(&a.flags->err, ERRBIT_TIMEOUT);
+                    s_abort = 1;
+                    break;
+                }
+                __nanosleep(100);
+            }
+            __threadfence();
+        }
         __syncthreads();
+        if (s_abort) {
+            // drain: mark this tile finished so that nothing waits on it
+            if (threadIdx.x == 0) {
+                const int64_t rem = tile % a.ntiles1;
+                for (int j = 0; j < Nm; ++j) {
+                    const int Ij = (int)((rem / a.TS[j]) % a.Bc[j]);
+                    if (Ij > 0) atomicSub(a.cnt + tile - a.TS[j], 1);
+                }
+            }
+            __syncthreads();
+            continue;
+        }
+
+        // stage 1a': strips of the modes outside the tile (solved tiles), entry
+        // by entry
+        if (npair > 0) {
+            for (int e = threadIdx.x; e < a.Pt; e += nt) {
+                int64_t g = gbase;
+                bool ok = true;
+                if (fastc) {
+                    const unsigned long long c = coord_s[e];
+                    for (int q = 0; q < nin; ++q) {
+                        const int t = (int)((c >> a.cshift[q]) & a.cmask[q]);
+                        if (partial && t >= s_be[a.inmode[q]]) { ok = false; break; }
+                        g += (int64_t)t * a.S[a.inmode[q]];
+                    }
+                } else {
+                    int r = e;
+                    for (int q = 0; q < nin; ++q) {
+                        const int j = a.inmode[q];
+                        const int t = r % a.b[j];
+                        r /= a.b[j];
+                        if (t >= s_be[j]) { ok = false; break; }
+                        g += (int64_t)t * a.S[j];
+                    }
+                }
+                if (!ok) continue;
+                YT acc{};
+                for (int p0 = 0; p0 < npair; p0 += 4) {        // 4 strip loads in flight
+                    YT y[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (p0 + u < npair) y[u] = __ldcg(Y + g + s_pstride[p0 + u]);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (p0 + u < npair) cmsub(acc, s_pt[p0 + u], y[u]);
+                }
+                add_to(tile_s[e], acc);
+            }
+            __syncthreads();
+        }
 
         // stage 1b: contributions of the solved tiles, mode by mode
         for (int j = 0; j < Nm; ++j) {
