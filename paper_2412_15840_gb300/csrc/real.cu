@@ -11,6 +11,7 @@
 // of one column, so every staged entry it loads feeds RB multiply-adds.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "cplx.cuh"
@@ -191,6 +192,106 @@ __global__ void __launch_bounds__(256) k_modeprod_r(const __grid_constant__ MPAr
     }
 }
 
+// The first mode (L = 1) in FP32: out[:, c] = M in[:, c] for every column c of
+// the n x (ntot nrhs / n) view.  A CTA keeps M (n x n) in shared memory and
+// walks tiles of CT1 columns: the tile is staged transposed (column index
+// fastest, rows padded to CT1 + 4 floats), and each thread computes 4 x 4
+// outputs from one float4 of M and one float4 of the tile per k.  Needs n a
+// multiple of 4, n <= MODE1_NMAX.
+constexpr int CT1 = 64;
+constexpr int CT1P = CT1 + 4;
+constexpr int MODE1_NMAX = 128;
+
+template <typename Tin, typename Tout, int EPI>
+__global__ void __launch_bounds__(256) k_mode1_r(const __grid_constant__ MPArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (a.done && *(volatile const int *)a.done) return;
+    const int n = a.gn[0];
+    float *Ms = reinterpret_cast<float *>(smem_raw);        // n x n, column-major
+    float *Xs = Ms + n * n;                                 // n rows of CT1P floats
+    const float *M = reinterpret_cast<const float *>(a.mats[0]);
+    for (int i = threadIdx.x; i < n * n; i += blockDim.x) Ms[i] = __ldg(M + i);
+    const Tin *in = reinterpret_cast<const Tin *>(a.in);
+    const int64_t cols = a.R;                               // columns of the view
+    const int64_t tiles = (cols + CT1 - 1) / CT1;
+    const int nq = n / 4;
+    const int items = nq * (CT1 / 4);
+    float nd = 0.f, nx = 0.f;
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int64_t c0 = tile * CT1;
+        const int cv = (int)(cols - c0 < CT1 ? cols - c0 : CT1);
+        __syncthreads();                                    // Xs of the previous tile consumed
+        const Tin *src = in + c0 * n;
+        for (int base = 0; base < n * CT1; base += 8 * 256) {
+            Tin v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int idx = base + u * 256 + (int)threadIdx.x;
+                v[u] = (idx < n * cv) ? src[idx] : Tin(0);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int idx = base + u * 256 + (int)threadIdx.x;
+                if (idx < n * CT1) Xs[(idx % n) * CT1P + idx / n] = (float)v[u];
+            }
+        }
+        __syncthreads();
+        for (int it = threadIdx.x; it < items; it += blockDim.x) {
+            const int ri = it % nq, ci = it / nq;
+            float acc[4][4] = {};
+            const float *mp = Ms + 4 * ri;
+            const float *xp = Xs + 4 * ci;
+            for (int k = 0; k < n; ++k) {
+                const float4 m = *reinterpret_cast<const float4 *>(mp + k * n);
+                const float4 x = *reinterpret_cast<const float4 *>(xp + k * CT1P);
+                const float mv[4] = {m.x, m.y, m.z, m.w}, xv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(mv[r], xv[c], acc[r][c]);
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int col = 4 * ci + c;
+                if (col >= cv) continue;
+                const int64_t g = (c0 + col) * n + 4 * ri;
+                if (EPI == EPI_STORE) {
+                    if constexpr (sizeof(Tout) == 4) {
+                        *reinterpret_cast<float4 *>(reinterpret_cast<float *>(a.out) + g) =
+                            make_float4(acc[0][c], acc[1][c], acc[2][c], acc[3][c]);
+                    } else {
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) reinterpret_cast<Tout *>(a.out)[g + r] = (Tout)acc[r][c];
+                    }
+                } else {
+                    double *Xp = reinterpret_cast<double *>(a.out);
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        const double d = (double)acc[r][c];
+                        if (EPI == EPI_STORE_NORM) {
+                            Xp[g + r] = d;
+                            nx = fmaxf(nx, absf(d));
+                        } else {
+                            const double x = Xp[g + r] + d;
+                            Xp[g + r] = x;
+                            nd = fmaxf(nd, absf(d));
+                            nx = fmaxf(nx, absf(x));
+                        }
+                    }
+                }
+            }
+        }
+    }
+    if (EPI == EPI_STORE_NORM || EPI == EPI_ACCUM) {
+        nd = warp_max(nd);
+        nx = warp_max(nx);
+        if ((threadIdx.x & 31) == 0) {
+            if (EPI == EPI_ACCUM) atomic_max_nonneg(&a.flags->dmax, nd);
+            atomic_max_nonneg(&a.flags->xmax, nx);
+        }
+    }
+}
+
 template <typename real, typename Tin, typename Tout, int EPI>
 cudaError_t set_attr() {
     return cudaFuncSetAttribute(k_modeprod_r<real, Tin, Tout, EPI>,
@@ -214,6 +315,27 @@ cudaError_t launch_modeprod_real(int fp64, int in_kind, int out_kind, int epi, c
         else
             return cudaErrorInvalidValue;
     } else {
+        // first mode (L = 1), one mode per pass, n a multiple of 4: the tiled kernel
+        if (a.G == 1 && a.L == 1 && a.gn[0] % 4 == 0 && a.gn[0] <= MODE1_NMAX) {
+            const int n = a.gn[0];
+            const size_t sm = (size_t)(n * n + n * CT1P) * sizeof(float);
+            const int64_t t1 = (a.R + CT1 - 1) / CT1;
+            int dev = 0, sms = 1;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            const unsigned g1 = (unsigned)std::max<int64_t>(1, std::min<int64_t>(t1, (int64_t)sms * 4));
+            if (epi == EPI_STORE && in_kind == ELEM_R64 && out_kind == ELEM_R32)
+                k_mode1_r<double, float, EPI_STORE><<<g1, block, sm, st>>>(a);
+            else if (epi == EPI_STORE && in_kind == ELEM_R32 && out_kind == ELEM_R32)
+                k_mode1_r<float, float, EPI_STORE><<<g1, block, sm, st>>>(a);
+            else if (epi == EPI_STORE_NORM && in_kind == ELEM_R32 && out_kind == ELEM_R64)
+                k_mode1_r<float, double, EPI_STORE_NORM><<<g1, block, sm, st>>>(a);
+            else if (epi == EPI_ACCUM && in_kind == ELEM_R32 && out_kind == ELEM_R64)
+                k_mode1_r<float, double, EPI_ACCUM><<<g1, block, sm, st>>>(a);
+            else
+                return cudaErrorInvalidValue;
+            return cudaGetLastError();
+        }
         if (epi == EPI_STORE && in_kind == ELEM_R64 && out_kind == ELEM_R32)
             k_modeprod_r<float, double, float, EPI_STORE><<<grid, block, smem, st>>>(a);
         else if (epi == EPI_STORE && in_kind == ELEM_R32 && out_kind == ELEM_R32)
@@ -235,7 +357,17 @@ cudaError_t modeprod_real_init_attrs() {
     if ((e = set_attr<float, double, float, EPI_STORE>()) != cudaSuccess) return e;
     if ((e = set_attr<float, float, float, EPI_STORE>()) != cudaSuccess) return e;
     if ((e = set_attr<float, float, double, EPI_STORE_NORM>()) != cudaSuccess) return e;
-    return set_attr<float, float, double, EPI_ACCUM>();
+    if ((e = set_attr<float, float, double, EPI_ACCUM>()) != cudaSuccess) return e;
+    const int big = 200 * 1024;
+    if ((e = cudaFuncSetAttribute(k_mode1_r<double, float, EPI_STORE>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_mode1_r<float, float, EPI_STORE>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_mode1_r<float, double, EPI_STORE_NORM>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess)
+        return e;
+    return cudaFuncSetAttribute(k_mode1_r<float, double, EPI_ACCUM>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, big);
 }
 
 }  // namespace sylv

@@ -42,7 +42,8 @@ def _solve(A, B, prec, **kw):
 @pytest.mark.parametrize("shape,nrhs,shift", [
     ((8, 8, 8), 1, 3.0), ((13, 1, 9, 4), 2, 3.0), ((2, 2, 3, 2, 2), 2, 2.0), ((64, 70), 1, 3.0),
     ((48, 5, 16), 3, 3.0), ((40, 2, 33), 1, 3.0), ((19, 19, 19), 1, 3.0), ((16, 17, 23), 2, 3.0),
-    ((7,), 4, 1.0), ((5, 1, 1, 6), 1, 2.0), ((2,) * 6, 1, 2.0), ((3, 2, 2, 2, 2, 2), 1, 2.0)])
+    ((7,), 4, 1.0), ((5, 1, 1, 6), 1, 2.0), ((2,) * 6, 1, 2.0), ((3, 2, 2, 2, 2, 2), 1, 2.0),
+    ((16,), 3, 2.0), ((12, 1), 70, 2.0), ((128, 6), 1, 3.0), ((36, 24, 4), 2, 3.0)])
 def test_real_solve_matches_oracle(shape, nrhs, shift, prec):
     p = si.random_real_problem(shape, nrhs, seed=len(shape) + nrhs, shift=shift)
     X, info, plan = _solve(p.A, p.B, prec)
