@@ -37,6 +37,8 @@ struct Group {
     // real plan: the pass runs on the complex view of the real tensor (pairs of
     // entries adjacent in memory as one complex entry; L counts those pairs)
     int cview = 0;
+    // FP64 residual group: three-multiplication products (re + im plane staged)
+    int g3 = 0;
 };
 
 // A mode after the first runs on the tensor cores when its fibres are at least
@@ -346,7 +348,7 @@ sylv_status make_groups(const sylv_plan_s &p, bool fp64, bool composition, int g
         g.first = 0; g.count = 0; g.L = 1; g.P = 1; g.R = tot;
         choose_tile(1, 1, tot, Et, Eh, g.Lt, g.Rt);
         g.tilesL = 1;
-        g.smem = (size_t)(g.Lt * g.Rt) * (esz + (plane ? 8 : 0));
+        g.smem = (size_t)(g.Lt * g.Rt) * esz;
         out.push_back(g);
         return SYLV_OK;
     }
@@ -392,10 +394,11 @@ sylv_status make_groups(const sylv_plan_s &p, bool fp64, bool composition, int g
         if (!choose_tile(g.L, g.P, g.R, Et, Eh, g.Lt, g.Rt)) return SYLV_ERR_SHAPE;
         g.tilesL = (g.L + g.Lt - 1) / g.Lt;
         int64_t E = (int64_t)g.Lt * g.P * g.Rt;
+        g.g3 = plane ? 1 : 0;
         // composition: two tiles (ping-pong); residual: the tile and its
         // re + im plane (FP64 only); otherwise one tile
         g.smem = (size_t)(E * esz * ((composition && g.count > 1) ? 2 : 1));
-        if (plane) g.smem += (size_t)E * 8;
+        if (g.g3) g.smem += (size_t)E * 8;
         if (g.smem > 200 * 1024) return SYLV_ERR_SHAPE;
         out.push_back(g);
         j += g.count;
@@ -740,6 +743,7 @@ cudaError_t run_residual(Ctx &c, const void *B, const void *X, void *R, const in
         a.sig_re = sg.real();
         a.sig_im = sg.imag();
         a.first = gi == 0;
+        a.g3 = g.g3;
         a.flags = c.flags;
         a.done = done;
         cudaError_t e = launch_modeprod(1, p->khi(), p->khi(), EPI_RESID, a, g.smem, c.st);

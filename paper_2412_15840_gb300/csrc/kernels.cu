@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(256) k_modeprod(const __grid_constant__ MPArgs
         C2 v = czero<C2>();
         if (l < lv && r < rv) v = to_c(in[(l0 + l) + L * ((int64_t)p + a.P * (r0 + r))], real());
         buf0[t] = v;
-        if (EPI == EPI_RESID) reinterpret_cast<real *>(buf1)[t] = v.x + v.y;
+        if (EPI == EPI_RESID && a.g3) reinterpret_cast<real *>(buf1)[t] = v.x + v.y;
     }
     __syncthreads();
 
@@ -161,8 +161,10 @@ __global__ void __launch_bounds__(256) k_modeprod(const __grid_constant__ MPArgs
         // Gauss's three-multiplication form of the complex product:
         //   Re = sum ar xr - sum ai xi,  Im = sum (ar + ai)(xr + xi) - sum ar xr - sum ai xi
         // with ar + ai stored after each matrix and xr + xi staged beside the
-        // tile, so every (i, k) term costs three FP64 FMAs instead of four.
+        // tile, so every (i, k) term costs three FP64 FMAs instead of four
+        // (a.g3; the classical product remains for callers without the plane).
         const real *bufS = reinterpret_cast<const real *>(buf1);
+        const bool g3 = a.g3 != 0;
         for (int t = threadIdx.x; t < E; t += blockDim.x) {
             int l = t % Lt;
             int rest = t / Lt;
@@ -181,19 +183,35 @@ __global__ void __launch_bounds__(256) k_modeprod(const __grid_constant__ MPArgs
                 const int64_t o = aa + (int64_t)bb * inner * nm;
                 const C2 *src = buf0 + o;
                 const real *srcS = bufS + o;
-                for (int k = 0; k < nm; ++k) {
-                    const C2 am = __ldg(M + i + k * nm);
-                    const real as = __ldg(MS + i + k * nm);
-                    const C2 x = src[k * inner];
-                    p1 = fma(am.x, x.x, p1);
-                    p2 = fma(am.y, x.y, p2);
-                    p3 = fma(as, srcS[k * inner], p3);
+                if (g3) {
+                    for (int k = 0; k < nm; ++k) {
+                        const C2 am = __ldg(M + i + k * nm);
+                        const real as = __ldg(MS + i + k * nm);
+                        const C2 x = src[k * inner];
+                        p1 = fma(am.x, x.x, p1);
+                        p2 = fma(am.y, x.y, p2);
+                        p3 = fma(as, srcS[k * inner], p3);
+                    }
+                } else {                   // classical: p1 = re, p2 = im, p3 unused
+                    for (int k = 0; k < nm; ++k) {
+                        const C2 am = __ldg(M + i + k * nm);
+                        const C2 x = src[k * inner];
+                        p1 = fma(am.x, x.x, p1);
+                        p1 = fma(-am.y, x.y, p1);
+                        p2 = fma(am.x, x.y, p2);
+                        p2 = fma(am.y, x.x, p2);
+                    }
                 }
                 inner *= nm;
             }
             C2 acc;
-            acc.x = p1 - p2;
-            acc.y = (p3 - p1) - p2;
+            if (g3) {
+                acc.x = p1 - p2;
+                acc.y = (p3 - p1) - p2;
+            } else {
+                acc.x = p1;
+                acc.y = p2;
+            }
             if (l < lv && r < rv) {
                 int64_t g = (l0 + l) + L * ((int64_t)p + a.P * (r0 + r));
                 double2 *Rp = reinterpret_cast<double2 *>(a.out);
@@ -267,7 +285,14 @@ __global__ void __launch_bounds__(256) k_modeprod(const __grid_constant__ MPArgs
             C2 acc[4];
             int tb;
             if constexpr (sizeof(real) == 8) {
-                if (rb == 4) tb = mode_rows_3m<4>(src, M, nm, inner, w, acc);
+                // three-multiplication products for modes with n >= 8; for small
+                // modes the extra loads and additions cost more than the saved
+                // multiplications (measured: n = 2 transform passes 23% slower)
+                if (nm < 8) {
+                    if (rb == 4) tb = mode_rows<4>(src, M, nm, inner, w, acc);
+                    else if (rb == 2) tb = mode_rows<2>(src, M, nm, inner, w, acc);
+                    else tb = mode_rows<1>(src, M, nm, inner, w, acc);
+                } else if (rb == 4) tb = mode_rows_3m<4>(src, M, nm, inner, w, acc);
                 else if (rb == 2) tb = mode_rows_3m<2>(src, M, nm, inner, w, acc);
                 else tb = mode_rows_3m<1>(src, M, nm, inner, w, acc);
             } else {

@@ -64,6 +64,8 @@ struct MPArgs {
     const void *B;
     double sig_re, sig_im;
     int first;
+    int g3;                   // FP64 residual: three-multiplication products (re + im
+                              // plane of X staged beside the tile); 0: classical
     // norms (float bits, max(|re|,|im|))
     DevFlags *flags;
     const int *done;          // early exit when *done != 0 (nullable)
