@@ -285,16 +285,16 @@ __global__ void __launch_bounds__(256) k_modeprod(const __grid_constant__ MPArgs
             C2 acc[4];
             int tb;
             if constexpr (sizeof(real) == 8) {
-                // three-multiplication products for modes with n >= 8; for small
-                // modes the extra loads and additions cost more than the saved
-                // multiplications (measured: n = 2 transform passes 23% slower)
-                if (nm < 8) {
+                // three-multiplication products for modes with n >= 8 and at least
+                // two rows per thread (the xr + xi addition is shared by the rows);
+                // otherwise the extra loads and additions cost more than the saved
+                // multiplications (measured: n = 2 passes 23% slower, n = 19 6%)
+                if (nm < 8 || rb == 1) {
                     if (rb == 4) tb = mode_rows<4>(src, M, nm, inner, w, acc);
                     else if (rb == 2) tb = mode_rows<2>(src, M, nm, inner, w, acc);
                     else tb = mode_rows<1>(src, M, nm, inner, w, acc);
                 } else if (rb == 4) tb = mode_rows_3m<4>(src, M, nm, inner, w, acc);
-                else if (rb == 2) tb = mode_rows_3m<2>(src, M, nm, inner, w, acc);
-                else tb = mode_rows_3m<1>(src, M, nm, inner, w, acc);
+                else tb = mode_rows_3m<2>(src, M, nm, inner, w, acc);
             } else {
                 if (rb == 4) tb = mode_rows<4>(src, M, nm, inner, w, acc);
                 else if (rb == 2) tb = mode_rows<2>(src, M, nm, inner, w, acc);
