@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
     // once per CTA (every tile uses the same tables)
     unsigned long long *coord_s = reinterpret_cast<unsigned long long *>(Td + a.tdsize);
     int *sched_s = reinterpret_cast<int *>(coord_s + (a.fast ? a.Pt : 0));
-    __shared__ int s_ticket, s_tile, s_abort, s_full;
+    __shared__ int s_ticket, s_tile, s_abort, s_full, s_hasfar;
     __shared__ int64_t s_o[MAXM];
     __shared__ int s_be[MAXM], s_cnt[MAXM], s_I[MAXM];
     __shared__ int64_t s_gbase, s_rhs0;
@@ -227,6 +227,11 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
                 np += K;
             }
             s_npair = np;
+            // columns beyond the immediate successor block in some mode
+            int hf = 0;
+            for (int j = 0; j < Nm; ++j)
+                if (!s_inlist[j] && s_cnt[j] > (a.qpos[j] >= 0 ? a.b[j] : 1)) hf = 1;
+            s_hasfar = hf;
         }
         __syncthreads();
         const int64_t gbase = s_gbase;
@@ -305,76 +310,9 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
             }
         }
 
-        // wait (bounded) until every immediate successor tile is solved
-        if (threadIdx.x == 0) {
-            volatile int *c = a.cnt + tile;
-            volatile int *err = &a.flags->err;
-            const long long t0 = clock64();
-            while (*c > 0) {
-                if (*err) { s_abort = 1; break; }
-                if (clock64() - t0 > a.timeout_cycles) {
-                    atomicOr(&a.flags->err, ERRBIT_TIMEOUT);
-                    s_abort = 1;
-                    break;
-                }
-                __nanosleep(100);
-            }
-            __threadfence();
-        }
-        __syncthreads();
-        if (s_abort) {
-            // drain: mark this tile finished so that nothing waits on it
-            if (threadIdx.x == 0) {
-                const int64_t rem = tile % a.ntiles1;
-                for (int j = 0; j < Nm; ++j) {
-                    const int Ij = (int)((rem / a.TS[j]) % a.Bc[j]);
-                    if (Ij > 0) atomicSub(a.cnt + tile - a.TS[j], 1);
-                }
-            }
-            __syncthreads();
-            continue;
-        }
-
-        // stage 1a': strips of the modes outside the tile (solved tiles), entry
-        // by entry
-        if (npair > 0) {
-            for (int e = threadIdx.x; e < a.Pt; e += nt) {
-                int64_t g = gbase;
-                bool ok = true;
-                if (fastc) {
-                    const unsigned long long c = coord_s[e];
-                    for (int q = 0; q < nin; ++q) {
-                        const int t = (int)((c >> a.cshift[q]) & a.cmask[q]);
-                        if (partial && t >= s_be[a.inmode[q]]) { ok = false; break; }
-                        g += (int64_t)t * a.S[a.inmode[q]];
-                    }
-                } else {
-                    int r = e;
-                    for (int q = 0; q < nin; ++q) {
-                        const int j = a.inmode[q];
-                        const int t = r % a.b[j];
-                        r /= a.b[j];
-                        if (t >= s_be[j]) { ok = false; break; }
-                        g += (int64_t)t * a.S[j];
-                    }
-                }
-                if (!ok) continue;
-                YT acc{};
-                for (int p0 = 0; p0 < npair; p0 += 4) {        // 4 strip loads in flight
-                    YT y[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        if (p0 + u < npair) y[u] = __ldcg(Y + g + s_pstride[p0 + u]);
-#pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        if (p0 + u < npair) cmsub(acc, s_pt[p0 + u], y[u]);
-                }
-                add_to(tile_s[e], acc);
-            }
-            __syncthreads();
-        }
-
-        // stage 1b: contributions of the solved tiles, mode by mode
+        // stage 1b: contributions of the solved tiles, mode by mode, over the columns
+        // of the immediate successor block (near) or beyond it (far)
+        auto strips = [&](bool far) {
         for (int j = 0; j < Nm; ++j) {
             const int K = s_cnt[j];
             if (K == 0 || s_inlist[j]) continue;
@@ -386,8 +324,10 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
             const int64_t nj = a.n[j], Sj = a.S[j], oj = s_o[j];
             const int64_t kend = oj + bej;
             const YT *Tj = reinterpret_cast<const YT *>(RL ? a.Tr[j] : a.T[j]);
-            for (int k0 = 0; k0 < K; k0 += SW_KCH) {
-                const int kk = min(SW_KCH, K - k0);
+            const int nb = min(bj, K);              // columns of the immediate successor
+            const int cb = far ? nb : 0, ce = far ? K : nb;
+            for (int k0 = cb; k0 < ce; k0 += SW_KCH) {
+                const int kk = min(SW_KCH, ce - k0);
                 for (int idx = threadIdx.x; idx < bej * kk; idx += nt) {
                     const int r = idx % bej, c = idx / bej;
                     Ts[c * bj + r] = __ldg(Tj + (oj + r) + (kend + k0 + c) * nj);
@@ -489,6 +429,119 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
                 __syncthreads();
             }
         }
+        };
+
+        // wait (bounded) until every immediate successor I + e_j whose mode has
+        // columns beyond it is ready to run: its counter is zero once all of its
+        // own successors are solved, among them I + m e_j for every m >= 2, so the
+        // far strips can be applied while the successors themselves still run
+        if (s_hasfar) {
+        if (threadIdx.x == 0) {
+            volatile int *err = &a.flags->err;
+            for (int j = 0; j < Nm && !s_abort; ++j) {
+                const int K = s_cnt[j];
+                if (K == 0 || s_inlist[j]) continue;
+                if (K <= (a.qpos[j] >= 0 ? a.b[j] : 1)) continue;
+                volatile int *c = a.cnt + tile + a.TS[j];
+                const long long t0 = clock64();
+                while (*c > 0) {
+                    if (*err) { s_abort = 1; break; }
+                    if (clock64() - t0 > a.timeout_cycles) {
+                        atomicOr(&a.flags->err, ERRBIT_TIMEOUT);
+                        s_abort = 1;
+                        break;
+                    }
+                    __nanosleep(100);
+                }
+            }
+            __threadfence();
+        }
+        __syncthreads();
+        if (s_abort) {
+            // drain: mark this tile finished so that nothing waits on it
+            if (threadIdx.x == 0) {
+                const int64_t rem = tile % a.ntiles1;
+                for (int j = 0; j < Nm; ++j) {
+                    const int Ij = (int)((rem / a.TS[j]) % a.Bc[j]);
+                    if (Ij > 0) atomicSub(a.cnt + tile - a.TS[j], 1);
+                }
+            }
+            __syncthreads();
+            continue;
+        }
+        strips(true);
+        }
+
+        // wait (bounded) until every immediate successor tile is solved
+        if (threadIdx.x == 0) {
+            volatile int *c = a.cnt + tile;
+            volatile int *err = &a.flags->err;
+            const long long t0 = clock64();
+            while (*c > 0) {
+                if (*err) { s_abort = 1; break; }
+                if (clock64() - t0 > a.timeout_cycles) {
+                    atomicOr(&a.flags->err, ERRBIT_TIMEOUT);
+                    s_abort = 1;
+                    break;
+                }
+                __nanosleep(100);
+            }
+            __threadfence();
+        }
+        __syncthreads();
+        if (s_abort) {
+            // drain: mark this tile finished so that nothing waits on it
+            if (threadIdx.x == 0) {
+                const int64_t rem = tile % a.ntiles1;
+                for (int j = 0; j < Nm; ++j) {
+                    const int Ij = (int)((rem / a.TS[j]) % a.Bc[j]);
+                    if (Ij > 0) atomicSub(a.cnt + tile - a.TS[j], 1);
+                }
+            }
+            __syncthreads();
+            continue;
+        }
+
+        // stage 1a': strips of the modes outside the tile (solved tiles), entry
+        // by entry
+        if (npair > 0) {
+            for (int e = threadIdx.x; e < a.Pt; e += nt) {
+                int64_t g = gbase;
+                bool ok = true;
+                if (fastc) {
+                    const unsigned long long c = coord_s[e];
+                    for (int q = 0; q < nin; ++q) {
+                        const int t = (int)((c >> a.cshift[q]) & a.cmask[q]);
+                        if (partial && t >= s_be[a.inmode[q]]) { ok = false; break; }
+                        g += (int64_t)t * a.S[a.inmode[q]];
+                    }
+                } else {
+                    int r = e;
+                    for (int q = 0; q < nin; ++q) {
+                        const int j = a.inmode[q];
+                        const int t = r % a.b[j];
+                        r /= a.b[j];
+                        if (t >= s_be[j]) { ok = false; break; }
+                        g += (int64_t)t * a.S[j];
+                    }
+                }
+                if (!ok) continue;
+                YT acc{};
+                for (int p0 = 0; p0 < npair; p0 += 4) {        // 4 strip loads in flight
+                    YT y[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (p0 + u < npair) y[u] = __ldcg(Y + g + s_pstride[p0 + u]);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (p0 + u < npair) cmsub(acc, s_pt[p0 + u], y[u]);
+                }
+                add_to(tile_s[e], acc);
+            }
+            __syncthreads();
+        }
+
+        strips(false);
 
         if constexpr (RL) rotate_pairs(a, tile_s, s_be, s_o, true);
 
