@@ -604,6 +604,9 @@ sylv_status build_sweep(const sylv_plan_s &p, const int *b, int threads, SweepCo
     if (ctas_per_sm > 0 && ctas_per_sm < per) per = ctas_per_sm;
     cfg.per_sm = per;
     cfg.grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)p.num_sms * per, a.ntiles));
+    // far strips ahead of the full dependency wait pay where the sweep is bound by
+    // its dependency chain: at most two tiles per level for each resident CTA
+    a.far_split = a.ntiles <= (int64_t)2 * cfg.grid * (maxlev + 1) ? 1 : 0;
     return SYLV_OK;
 }
 

@@ -312,7 +312,8 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
 
         // stage 1b: contributions of the solved tiles, mode by mode, over the columns
         // of the immediate successor block (near) or beyond it (far)
-        auto strips = [&](bool far) {
+        // part 0: all columns; 1: beyond the immediate successor block; 2: that block
+        auto strips = [&](int part) {
         for (int j = 0; j < Nm; ++j) {
             const int K = s_cnt[j];
             if (K == 0 || s_inlist[j]) continue;
@@ -325,7 +326,7 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
             const int64_t kend = oj + bej;
             const YT *Tj = reinterpret_cast<const YT *>(RL ? a.Tr[j] : a.T[j]);
             const int nb = min(bj, K);              // columns of the immediate successor
-            const int cb = far ? nb : 0, ce = far ? K : nb;
+            const int cb = part == 1 ? nb : 0, ce = part == 2 ? nb : K;
             for (int k0 = cb; k0 < ce; k0 += SW_KCH) {
                 const int kk = min(SW_KCH, ce - k0);
                 for (int idx = threadIdx.x; idx < bej * kk; idx += nt) {
@@ -434,8 +435,11 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
         // wait (bounded) until every immediate successor I + e_j whose mode has
         // columns beyond it is ready to run: its counter is zero once all of its
         // own successors are solved, among them I + m e_j for every m >= 2, so the
-        // far strips can be applied while the successors themselves still run
-        if (s_hasfar) {
+        // far strips can be applied while the successors themselves still run.
+        // Only when the sweep is latency-bound (few tiles per level for the
+        // resident CTAs): otherwise the extra staging passes cost throughput.
+        const bool split = a.far_split && s_hasfar;
+        if (split) {
         if (threadIdx.x == 0) {
             volatile int *err = &a.flags->err;
             for (int j = 0; j < Nm && !s_abort; ++j) {
@@ -469,7 +473,7 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
             __syncthreads();
             continue;
         }
-        strips(true);
+        strips(1);
         }
 
         // wait (bounded) until every immediate successor tile is solved
@@ -541,7 +545,7 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
             __syncthreads();
         }
 
-        strips(false);
+        strips(split ? 2 : 0);
 
         if constexpr (RL) rotate_pairs(a, tile_s, s_be, s_o, true);
 

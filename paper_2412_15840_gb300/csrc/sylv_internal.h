@@ -112,6 +112,7 @@ struct SweepArgs {
     // vectors V of the diagonal blocks, 4 complex entries (column-major) per
     // pair of indices (2u, 2u + 1), identity where both are 1 x 1 blocks; null
     // for a mode without 2 x 2 blocks
+    int far_split;            // strips beyond the successor block before the full wait
     int real;
     const void *Tr[MAXM];
     const void *Vp[MAXM];

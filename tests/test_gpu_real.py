@@ -162,3 +162,12 @@ def test_real_many_coupled_modes():
     # 14 such modes need a 2^14-entry tile: beyond the sweep's tile limit
     with pytest.raises(SylvError):
         Plan(A=A + A[:6], nrhs=1, prec="fp64", real=True)
+
+
+def test_real_singular_operator_is_refused():
+    # eigenvalues +-i in both modes: the sum i + (-i) of the Schur diagonals is zero
+    rot = np.array([[0.0, 1.0], [-1.0, 0.0]])
+    A = [np.kron(np.eye(2), rot), np.kron(np.eye(3), rot)]
+    with pytest.raises(SylvError) as ex:
+        Plan(A=A, nrhs=1, prec="fp64", real=True)
+    assert "SINGULAR" in str(ex.value)
