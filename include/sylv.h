@@ -16,7 +16,9 @@
  *  - Complex numbers are interleaved (re, im) pairs: complex128 = 2 doubles,
  *    complex64 = 2 floats.
  *  - Matrices (A_j, U_j, T_j) are column-major n_j x n_j complex128 in HOST
- *    memory: entry (a, b) is at [2*(a + b*n_j)].
+ *    memory: entry (a, b) is at [2*(a + b*n_j)].  The real-arithmetic
+ *    variant (sylv_plan_create_real) takes float64 A_j, entry (a, b) at
+ *    [a + b*n_j], and float64 / float32 tensors.
  *  - Tensors are column-major with i_1 fastest (Section 2.2, Eq. (index)) and
  *    live in DEVICE memory; a tensor with nrhs right-hand sides has one extra
  *    trailing index of extent nrhs (the right-hand sides are independent).
@@ -26,7 +28,8 @@
  *    cudaStream_t passed as void*; NULL = legacy default stream) and
  *    asynchronous unless stated.  No entry point throws; every failure is a
  *    sylv_status.  CUDA errors map to SYLV_ERR_CUDA.
- *  - The library allocates device memory only inside sylv_plan_create: the
+ *  - The library allocates device memory only inside sylv_plan_create (and
+ *    sylv_plan_create_real, sylv_plan_autotune for its candidate tables): the
  *    factors and tiling tables, and, when prod_j n_j * 16 bytes <= 1 GiB, a
  *    table of the sweep's FP64 reciprocals (one per multi-index; without it
  *    the sweep forms them on the fly).  Tensor-sized scratch memory
