@@ -171,3 +171,13 @@ def test_real_singular_operator_is_refused():
     with pytest.raises(SylvError) as ex:
         Plan(A=A, nrhs=1, prec="fp64", real=True)
     assert "SINGULAR" in str(ex.value)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_real_all_singleton_modes(prec):
+    # no mode to transform: X = B / (a_1 + a_2 + a_3)
+    A = [np.array([[2.0]]), np.array([[1.5]]), np.array([[-0.25]])]
+    B = si.real_gaussian(np.random.default_rng(8), (1, 1, 1, 6))
+    X, info, _ = _solve(A, B, prec)
+    assert info["status"] == 0
+    assert oracle.rel_err(X, B / 3.25) < TOL[prec]
