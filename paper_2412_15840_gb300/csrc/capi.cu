@@ -1,7 +1,9 @@
 // Host runtime and C ABI (include/sylv.h) of the N-dimensional Sylvester
-// solver: plan construction (Schur factors, transform pass grouping, sweep
-// tiling and schedules, workspace layout) and the stream-ordered launch
-// sequences of Algorithm 3 and of the mixed-precision refinement loop.
+// solver: plan construction (complex or real Schur factors, transform pass
+// grouping, sweep tiling and schedules, workspace layout) and the
+// stream-ordered launch sequences of Algorithm 3, of the mixed-precision
+// refinement loop (FP64 or tensor-core residual), of Theorem 1 (sylv_evolve),
+// of batched solves under one CUDA graph, and of the sweep autotuner.
 #include <cuda_runtime.h>
 
 #include <algorithm>

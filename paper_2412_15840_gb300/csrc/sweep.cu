@@ -14,17 +14,24 @@
 //
 // One tile, three stages:
 //  1. load C, form the FP64 reciprocal of sigma + sum_j t_{j,i_j i_j} for
-//     every entry (or read it from the plan's table) and subtract, entry by
-//     entry, the strips of the modes outside the tile; then subtract the
-//     contributions of the solved tiles along the in-tile modes, mode by mode,
-//     as a small GEMM: T_j[rows of the block, later columns] times the strip of
-//     solved values.  A fiber of the tile along mode j belongs to one thread
-//     (or a few adjacent lanes), which loads every strip value once and applies
-//     all b_j rows of the T block (staged in shared memory) to it.
+//     every entry (or read it from the plan's table) and the diagonal T blocks
+//     -- the tile's own data, loaded before the dependency wait; subtract,
+//     entry by entry, the strips of the modes outside the tile; then subtract
+//     the contributions of the solved tiles along the in-tile modes, mode by
+//     mode, as a small GEMM: T_j[rows of the block, later columns] times the
+//     strip of solved values.  A fiber of the tile along mode j belongs to one
+//     thread (or a few adjacent lanes), which loads every strip value once and
+//     applies all b_j rows of the T block (staged in shared memory) to it.
+//     Where the sweep is latency-bound, the columns beyond the immediate
+//     successor block are applied first, as soon as each successor I + e_j is
+//     ready to run (its own counter is zero, so every I + m e_j with m >= 2 is
+//     solved), and the successor block after the full wait.
 //  2. solve the tile in place, level by level of the in-tile index sum
 //     measured from the tile's end: the in-tile part of Eq. (yi1i2iN), then
 //     y = num * (1/den) with the reciprocal formed in FP64 in stage 1.
 //  3. store Y (L2), fence, release the counters of the predecessor tiles.
+// The real-arithmetic variant (RL) keeps C, Y and the strips real and rotates
+// the tile's 2 x 2 blocks to complex triangular form around stage 2.
 #include <cuda_runtime.h>
 
 #include <algorithm>
