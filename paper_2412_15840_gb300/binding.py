@@ -239,7 +239,9 @@ class Plan:
             raise ValueError("a real plan takes A only")
         if (A is None) == (Q is None or T is None) and not self.real:
             raise ValueError("give A, or both Q and T")
-        mats = [np.atleast_2d(np.asarray(a, dtype=np.float64)) if self.real else _cmat(a)
+        if self.real and any(np.iscomplexobj(a) and np.any(np.imag(a) != 0) for a in A):
+            raise ValueError("a real plan takes real A_j (an operator has imaginary parts)")
+        mats = [np.atleast_2d(np.asarray(np.real(a), dtype=np.float64)) if self.real else _cmat(a)
                 for a in (A if A is not None else T)]
         self.shape = tuple(int(m.shape[0]) for m in mats)
         self.N = len(self.shape)

@@ -199,3 +199,12 @@ def test_host_expm_rejects_bad_input():
     with pytest.raises(binding.SylvError) as e:
         pkg.expm(np.array([[np.nan]]))
     assert e.value.status == 1
+
+
+def test_real_plan_refuses_complex_operators():
+    # checked in the binding before any device call
+    A = [np.eye(3) * (2.0 + 0.5j), np.eye(2)]
+    with pytest.raises(ValueError):
+        pkg.Plan(A=A, nrhs=1, prec="fp64", real=True)
+    with pytest.raises(ValueError):
+        pkg.Plan(Q=[np.eye(3)], T=[np.eye(3)], nrhs=1, real=True)
