@@ -371,13 +371,22 @@ class Plan:
         _check(s, "sylv_evolve")
         return X
 
+    def _check_tensor(self, t, dtype, what):
+        # the library reads and writes prod(shape) * nrhs elements of the plan's
+        # element type: a tensor of another type or size would be overrun
+        if t.dtype != dtype or t.numel() != self.numel or not t.is_cuda:
+            raise ValueError(f"{what} must be a CUDA {dtype} tensor with prod(shape)*nrhs "
+                             f"= {self.numel} elements")
+
     def forward(self, Tns, workspace=None, stream=None):
+        self._check_tensor(Tns, self.work_dtype, "the tensor")
         wp, wb = self._wsargs(workspace)
         _check(_lib().sylv_forward(self._h, _ptr(Tns), wp, wb, _stream_handle(stream)),
                "sylv_forward")
         return Tns
 
     def sweep(self, Tns, workspace=None, stream=None):
+        self._check_tensor(Tns, self.work_dtype, "the tensor")
         wp, wb = self._wsargs(workspace)
         _check(_lib().sylv_sweep(self._h, _ptr(Tns), wp, wb, _stream_handle(stream)),
                "sylv_sweep")
@@ -386,11 +395,13 @@ class Plan:
     def sweep_static(self, Tns, stream=None):
         """sylv_sweep_static: the sweep with the library's fixed scratch array
         (no workspace, no allocation); see include/sylv.h for its limits."""
+        self._check_tensor(Tns, self.work_dtype, "the tensor")
         _check(_lib().sylv_sweep_static(self._h, _ptr(Tns), _stream_handle(stream)),
                "sylv_sweep_static")
         return Tns
 
     def back(self, Tns, workspace=None, stream=None):
+        self._check_tensor(Tns, self.work_dtype, "the tensor")
         wp, wb = self._wsargs(workspace)
         _check(_lib().sylv_back(self._h, _ptr(Tns), wp, wb, _stream_handle(stream)),
                "sylv_back")
@@ -400,6 +411,8 @@ class Plan:
         import torch
         if R is None:
             R = torch.empty_like(B)
+        for t, what in ((B, "B"), (X, "X"), (R, "R")):
+            self._check_tensor(t, self.dtype, what)
         _check(_lib().sylv_residual(self._h, _ptr(B), _ptr(X), _ptr(R), _stream_handle(stream)),
                "sylv_residual")
         return R
@@ -411,6 +424,7 @@ class Plan:
         if scratch is None:
             scratch = torch.empty(self.numel, dtype=self.work_dtype,
                                   device=f"cuda:{self.device}")
+        self._check_tensor(scratch, self.work_dtype, "the scratch tensor")
         wp, wb = self._wsargs(workspace)
         blk = (ctypes.c_int32 * self.N)()
         ms = ctypes.c_float()
