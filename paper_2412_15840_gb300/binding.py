@@ -327,10 +327,10 @@ class Plan:
         """X with sum_j A_j (x)_j X = B; B, X flat complex128 (float64 for a real
         plan) device tensors."""
         import torch
-        if B.dtype != self.dtype or B.numel() != self.numel:
-            raise ValueError(f"B must be {self.dtype} with prod(shape)*nrhs elements")
+        self._check_tensor(B, self.dtype, "B")
         if X is None:
             X = torch.empty_like(B)
+        self._check_tensor(X, self.dtype, "X")
         wp, wb = self._wsargs(workspace)
         inf = Info() if info else None
         s = _lib().sylv_solve(self._h, _ptr(B), _ptr(X), wp, wb, _stream_handle(stream),
@@ -352,11 +352,11 @@ class Plan:
         """X(t) of X_t = sum_j A_j (x)_j X + B, X(0) = X0 (Theorem 1); flat complex128
         device tensors.  `workspace` holds at least evolve_workspace_bytes()."""
         import torch
-        for v in (B, X0):
-            if v.dtype != torch.complex128 or v.numel() != self.numel:
-                raise ValueError("B and X0 must be complex128 with prod(shape)*nrhs elements")
+        for v, what in ((B, "B"), (X0, "X0")):
+            self._check_tensor(v, torch.complex128, what)
         if X is None:
             X = torch.empty_like(B)
+        self._check_tensor(X, torch.complex128, "X")
         if workspace is None:
             workspace = torch.empty(self.evolve_workspace_bytes(), dtype=torch.uint8,
                                     device=f"cuda:{self.device}")
@@ -475,6 +475,9 @@ def solve_batched(plans: Sequence[Plan], Bs: Sequence, Xs: Sequence, workspace, 
                   info: bool = False):
     """sylv_solve_batched over independent equations (any shapes)."""
     m = len(plans)
+    for p, b, x in zip(plans, Bs, Xs):
+        p._check_tensor(b, p.dtype, "B")
+        p._check_tensor(x, p.dtype, "X")
     hs = (vp * m)(*[p.handle for p in plans])
     pb = (vp * m)(*[_ptr(b) for b in Bs])
     px = (vp * m)(*[_ptr(x) for x in Xs])
