@@ -208,3 +208,39 @@ def test_real_plan_refuses_complex_operators():
         pkg.Plan(A=A, nrhs=1, prec="fp64", real=True)
     with pytest.raises(ValueError):
         pkg.Plan(Q=[np.eye(3)], T=[np.eye(3)], nrhs=1, real=True)
+
+
+@pytest.mark.parametrize("kind", ["orthogonal", "large", "scaled_small", "scaled_large",
+                                  "defective_pairs", "companion"])
+def test_host_real_schur_stress(kind):
+    rng = np.random.default_rng(7 * len(kind) + ord(kind[0]))
+    if kind == "orthogonal":            # every eigenvalue on the unit circle: mostly pairs
+        A, _ = np.linalg.qr(rng.standard_normal((40, 40)))
+    elif kind == "large":
+        A = rng.standard_normal((130, 130)) / np.sqrt(130)
+    elif kind == "scaled_small":
+        A = 1e-8 * rng.standard_normal((25, 25))
+    elif kind == "scaled_large":
+        A = 1e8 * rng.standard_normal((25, 25))
+    elif kind == "defective_pairs":     # a 2 x 2 rotation block repeated in a Jordan chain
+        R = np.array([[1.0, 2.0], [-2.0, 1.0]])
+        A = np.kron(np.eye(4), R) + np.kron(np.eye(4, k=1), np.eye(2))
+        Q, _ = np.linalg.qr(rng.standard_normal((8, 8)))
+        A = Q @ A @ Q.T
+    else:                               # companion matrix of a polynomial with complex roots
+        roots = np.concatenate([np.exp(1j * np.linspace(0.3, 2.8, 6)) * 1.5,
+                                np.exp(-1j * np.linspace(0.3, 2.8, 6)) * 1.5, [0.7, -1.2]])
+        c = np.real(np.poly(roots))
+        n = len(c) - 1
+        A = np.zeros((n, n))
+        A[0, :] = -c[1:] / c[0]
+        A[1:, :-1] = np.eye(n - 1)
+    Q, T = pkg.schur_real(A)
+    n = A.shape[0]
+    scale = np.abs(A).max()
+    assert np.abs(Q.T @ Q - np.eye(n)).max() < 1e-12 * n
+    assert np.abs(Q @ T @ Q.T - A).max() < 1e-12 * n * scale
+    assert np.abs(np.tril(T, -2)).max(initial=0.0) == 0.0
+    assert all(T[k + 1, k] == 0.0 for k in range(1, n - 1, 2))
+    if kind != "defective_pairs":       # (a defective spectrum is ill-conditioned)
+        _check_real_schur(A, Q, T, tol=1e-11 if kind != "companion" else 1e-9)
