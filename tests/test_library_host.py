@@ -244,3 +244,26 @@ def test_host_real_schur_stress(kind):
     assert all(T[k + 1, k] == 0.0 for k in range(1, n - 1, 2))
     if kind != "defective_pairs":       # (a defective spectrum is ill-conditioned)
         _check_real_schur(A, Q, T, tol=1e-11 if kind != "companion" else 1e-9)
+
+
+@pytest.mark.parametrize("kind", ["unitary", "large", "scaled_small", "scaled_large", "jordan"])
+def test_host_schur_stress(kind):
+    rng = np.random.default_rng(11 * len(kind) + ord(kind[0]))
+    if kind == "unitary":
+        A, _ = np.linalg.qr(rng.standard_normal((40, 40)) + 1j * rng.standard_normal((40, 40)))
+    elif kind == "large":
+        A = (rng.standard_normal((130, 130)) + 1j * rng.standard_normal((130, 130))) / 12
+    elif kind == "scaled_small":
+        A = 1e-8 * (rng.standard_normal((25, 25)) + 1j * rng.standard_normal((25, 25)))
+    elif kind == "scaled_large":
+        A = 1e8 * (rng.standard_normal((25, 25)) + 1j * rng.standard_normal((25, 25)))
+    else:                               # a Jordan block in a random unitary basis
+        J = (1.0 + 2.0j) * np.eye(9) + np.eye(9, k=1)
+        Q, _ = np.linalg.qr(rng.standard_normal((9, 9)) + 1j * rng.standard_normal((9, 9)))
+        A = Q @ J @ Q.conj().T
+    Q, T = pkg.schur(A)
+    n = A.shape[0]
+    scale = np.abs(A).max()
+    assert np.abs(Q.conj().T @ Q - np.eye(n)).max() < 1e-12 * n
+    assert np.abs(Q @ T @ Q.conj().T - A).max() < 1e-12 * n * scale
+    assert np.abs(np.tril(T, -1)).max() == 0.0
