@@ -292,11 +292,16 @@ sylv_status sylv_residual(sylv_plan_t plan, const void *B_dev, const void *X_dev
  * GPU that loads the library holds until the process exits; nothing is
  * allocated and no workspace is passed.  T_dev is as for sylv_sweep (plan's
  * working precision, in place).
- *  - Plans whose sweep needs more than SYLV_STATIC_SCRATCH_BYTES
- *    (64 + 4 * tiles, rounded up to 256) are rejected with SYLV_ERR_SHAPE.
+ *  - The tiled sweep needs 256 bytes for the control block plus 4 bytes per
+ *    tile rounded up to 256, i.e. at most 262,080 tiles in the 1 MiB array;
+ *    plans with more tiles are rejected with SYLV_ERR_SHAPE.  A plan whose
+ *    sweep is the entrywise division of Remark 1 (sylv_info.path bit 0)
+ *    needs the control block only and is never refused for its size.
  *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.
+ *    (cudaGetSymbolAddress) with that device current and keeps it for the
+ *    life of the process; make that first call before any stream capture.
+ *    Calls after a cudaDeviceReset of that device are not supported (the
+ *    kept address belongs to the destroyed context).
  *  - Every call on a device shares the one array and leaves its contents
  *    behind; each call clears what must start at zero before it sweeps.
  *    Calls whose work overlaps on the GPU (other streams, other threads,

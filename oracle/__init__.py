@@ -38,4 +38,5 @@ from .bartels_stewart import (  # noqa: F401
     evolve_rhs,
     rel_err,
     backward_error,
+    set_threads,
 )

@@ -39,6 +39,11 @@ def _lib():
         lib.oracle_sweep.restype = ctypes.c_int
         lib.oracle_sweep.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
                                      ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p]
+        lib.oracle_mode_product.restype = ctypes.c_int
+        lib.oracle_mode_product.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        lib.oracle_set_threads.restype = None
+        lib.oracle_set_threads.argtypes = [ctypes.c_int]
         lib.oracle_counter_order.restype = ctypes.c_int
         lib.oracle_counter_order.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
                                              ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
@@ -78,11 +83,37 @@ def counter_order(n: Sequence[int], count: Optional[int] = None) -> List[Tuple[i
 # ----------------------------------------------------------------------------
 
 def mode_product(M: np.ndarray, X: np.ndarray, j: int) -> np.ndarray:
-    """[M (x)_j X]_{..i..} = sum_k M[i, k] X[..k..] along axis j (0-based)."""
+    """[M (x)_j X]_{..i..} = sum_k M[i, k] X[..k..] along axis j (0-based).
+
+    X (column-major) is viewed as (L, n_j, R) with L = prod_{m<j} n_m and
+    R = prod_{m>j} n_m, so that out[l, i, r] = sum_k M[i, k] X[l, k, r]:
+    complex data in oracle/modeprod.c (plain loops, k ascending), real data
+    (the real-arithmetic variant) as one library matrix product per slice over
+    the shorter of L and R."""
     if M.shape == (1, 1):
         return M[0, 0] * X                                  # scalar case, Section 4
-    out = np.tensordot(M, X, axes=([1], [j]))              # new axis 0 is i
-    return np.asfortranarray(np.moveaxis(out, 0, j))
+    X = np.asfortranarray(X)
+    shp = X.shape
+    L = int(np.prod(shp[:j], dtype=np.int64))
+    n = int(shp[j])
+    R = int(np.prod(shp[j + 1:], dtype=np.int64))
+    if np.iscomplexobj(M) or np.iscomplexobj(X):
+        Mc = np.asfortranarray(M, dtype=np.complex128)
+        Xc = np.asfortranarray(X, dtype=np.complex128)
+        out = np.empty(shp, dtype=np.complex128, order="F")
+        if _lib().oracle_mode_product(L, n, R, Mc.ctypes.data, Xc.ctypes.data,
+                                      out.ctypes.data) != 0:
+            raise RuntimeError("oracle_mode_product: bad arguments")
+        return out
+    X3 = X.reshape((L, n, R), order="F")
+    out = np.empty((L, n, R), dtype=np.result_type(M, X), order="F")
+    if L >= R:
+        for r in range(R):
+            out[:, :, r] = X3[:, :, r] @ M.T                # out[l, i] = sum_k X[l, k] M[i, k]
+    else:
+        for l in range(L):
+            out[l, :, :] = M @ X3[l, :, :]                  # out[i, r] = sum_k M[i, k] X[k, r]
+    return out.reshape(shp, order="F")
 
 
 def apply_operator(A: Sequence[np.ndarray], X: np.ndarray) -> np.ndarray:
@@ -247,6 +278,13 @@ def evolve(A: Sequence[np.ndarray], B: np.ndarray, X0: np.ndarray, t: float) -> 
     the Sylvester equation sum_j A_j (x)_j X(t) = F, Eq. (sylvesterNDC)-(C), by
     Algorithm 3."""
     return solve(A, evolve_rhs(A, B, X0, t))
+
+
+def set_threads(k: int) -> None:
+    """Threads that the calling thread's mode products spread their independent
+    fibres over (1: stay on the calling thread, for callers that run several
+    oracle solves at once)."""
+    _lib().oracle_set_threads(int(k))
 
 
 # ----------------------------------------------------------------------------

@@ -205,6 +205,28 @@ def _ptr(t) -> int:
     return t.data_ptr()
 
 
+def check_tensor(t, dtype, numel: int, device: int, what: str):
+    """Refuse a tensor the library would misuse: it reads and writes `numel`
+    elements of `dtype` on the plan's device, so a tensor of another type or
+    size would be overrun, and one on another GPU would be dereferenced from
+    the plan's device (an illegal address without peer access)."""
+    if t.dtype != dtype or t.numel() != numel or not t.is_cuda:
+        raise ValueError(f"{what} must be a CUDA {dtype} tensor with prod(shape)*nrhs "
+                         f"= {numel} elements")
+    if t.device.index is not None and t.device.index != device:
+        raise ValueError(f"{what} is on cuda:{t.device.index}, the plan on cuda:{device}")
+
+
+def check_workspace(ws, device: int, what: str = "workspace"):
+    """A workspace is device memory of the plan's GPU (any dtype, contiguous)."""
+    if not ws.is_cuda:
+        raise ValueError(f"{what} must be a CUDA tensor on cuda:{device}")
+    if ws.device.index is not None and ws.device.index != device:
+        raise ValueError(f"{what} is on cuda:{ws.device.index}, the plan on cuda:{device}")
+    if not ws.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+
+
 def to_device(x: np.ndarray, device="cuda", dtype=None):
     """numpy array (logical shape, any order) -> flat device tensor in column-major order."""
     import torch
@@ -307,6 +329,7 @@ class Plan:
 
     def _wsargs(self, workspace):
         ws = self.workspace() if workspace is None else workspace
+        check_workspace(ws, self.device, "workspace")
         return ws.data_ptr(), ws.numel() * ws.element_size()
 
     @property
@@ -360,6 +383,7 @@ class Plan:
         if workspace is None:
             workspace = torch.empty(self.evolve_workspace_bytes(), dtype=torch.uint8,
                                     device=f"cuda:{self.device}")
+        check_workspace(workspace, self.device, "workspace")
         inf = Info() if info else None
         s = _lib().sylv_evolve(self._h, float(t), _ptr(B), _ptr(X0), _ptr(X),
                                workspace.data_ptr(), workspace.numel(), _stream_handle(stream),
@@ -372,11 +396,7 @@ class Plan:
         return X
 
     def _check_tensor(self, t, dtype, what):
-        # the library reads and writes prod(shape) * nrhs elements of the plan's
-        # element type: a tensor of another type or size would be overrun
-        if t.dtype != dtype or t.numel() != self.numel or not t.is_cuda:
-            raise ValueError(f"{what} must be a CUDA {dtype} tensor with prod(shape)*nrhs "
-                             f"= {self.numel} elements")
+        check_tensor(t, dtype, self.numel, self.device, what)
 
     def forward(self, Tns, workspace=None, stream=None):
         self._check_tensor(Tns, self.work_dtype, "the tensor")
@@ -475,9 +495,13 @@ def solve_batched(plans: Sequence[Plan], Bs: Sequence, Xs: Sequence, workspace, 
                   info: bool = False):
     """sylv_solve_batched over independent equations (any shapes)."""
     m = len(plans)
+    if len(Bs) != m or len(Xs) != m:
+        raise ValueError("plans, Bs and Xs must have the same length")
     for p, b, x in zip(plans, Bs, Xs):
         p._check_tensor(b, p.dtype, "B")
         p._check_tensor(x, p.dtype, "X")
+    if m:
+        check_workspace(workspace, plans[0].device, "workspace")
     hs = (vp * m)(*[p.handle for p in plans])
     pb = (vp * m)(*[_ptr(b) for b in Bs])
     px = (vp * m)(*[_ptr(x) for x in Xs])

@@ -2079,7 +2079,10 @@ sylv_status static_scratch(int dev, void **out) {
 extern "C" sylv_status sylv_sweep_static(sylv_plan_t p, void *Tdev, void *stream) {
     if (!p || !Tdev) return SYLV_ERR_INVALID_ARG;
     const size_t cnt_off = align256(sizeof(DevFlags));
-    if (cnt_off + align256((size_t)p->sweep.a.ntiles * 4) > SYLV_STATIC_SCRATCH_BYTES)
+    // the entrywise-division sweep (Remark 1) uses the control block only; the
+    // tiled sweep also one int counter per tile
+    if (!p->diag_sweep &&
+        cnt_off + align256((size_t)p->sweep.a.ntiles * 4) > SYLV_STATIC_SCRATCH_BYTES)
         return SYLV_ERR_SHAPE;
     DeviceGuard dg(p->device);
     if (!dg.ok) return SYLV_ERR_CUDA;

@@ -267,3 +267,45 @@ def test_host_schur_stress(kind):
     assert np.abs(Q.conj().T @ Q - np.eye(n)).max() < 1e-12 * n
     assert np.abs(Q @ T @ Q.conj().T - A).max() < 1e-12 * n * scale
     assert np.abs(np.tril(T, -1)).max() == 0.0
+
+
+class _FakeCudaTensor:
+    """Duck-typed stand-in for a CUDA tensor (no GPU here): only the attributes
+    the binding's argument checks read."""
+
+    def __init__(self, dtype, numel, index, contiguous=True):
+        import torch
+        self.dtype = dtype
+        self._numel = numel
+        self.is_cuda = True
+        self.device = torch.device("cuda", index)
+        self._contiguous = contiguous
+
+    def numel(self):
+        return self._numel
+
+    def is_contiguous(self):
+        return self._contiguous
+
+
+def test_binding_refuses_tensors_on_another_device():
+    # the library would dereference such a tensor from the plan's GPU: the
+    # binding refuses it before any call reaches the library
+    torch = pytest.importorskip("torch")
+    c128 = torch.complex128
+    binding.check_tensor(_FakeCudaTensor(c128, 8, 1), c128, 8, 1, "B")       # accepted
+    with pytest.raises(ValueError, match="cuda:1"):
+        binding.check_tensor(_FakeCudaTensor(c128, 8, 1), c128, 8, 0, "B")
+    with pytest.raises(ValueError):
+        binding.check_tensor(_FakeCudaTensor(c128, 7, 0), c128, 8, 0, "B")   # size
+    with pytest.raises(ValueError):
+        binding.check_tensor(_FakeCudaTensor(torch.complex64, 8, 0), c128, 8, 0, "B")
+    with pytest.raises(ValueError):
+        binding.check_tensor(torch.zeros(8, dtype=c128), c128, 8, 0, "B")    # host tensor
+    binding.check_workspace(_FakeCudaTensor(torch.uint8, 256, 2), 2)
+    with pytest.raises(ValueError, match="cuda:2"):
+        binding.check_workspace(_FakeCudaTensor(torch.uint8, 256, 2), 0)
+    with pytest.raises(ValueError):
+        binding.check_workspace(_FakeCudaTensor(torch.uint8, 256, 0, contiguous=False), 0)
+    with pytest.raises(ValueError):
+        binding.check_workspace(torch.zeros(256, dtype=torch.uint8), 0)
