@@ -62,6 +62,9 @@ def parse():
                     help="skip the oracle error check and CPU baseline")
     ap.add_argument("--kernels-once", action="store_true",
                     help="run each hot-path kernel family once on the workload (for ncu)")
+    ap.add_argument("--workloads", default="N3_n8,N29_n2,advdiff48,batch512,N7_n19",
+                    help="other configurations measured in the default run (comma list; "
+                         "'none' skips them)")
     ap.add_argument("--workload", default="n64_N4",
                     choices=["n64_N4", "batch512", "advdiff48", "n2_N29", "n19_N7",
                              "evolve_n64_N4", "real_n64_N4"],
@@ -71,11 +74,10 @@ def parse():
 
 
 def oracle_threads() -> int:
-    try:
-        from threadpoolctl import threadpool_info
-        return max([d.get("num_threads", 1) for d in threadpool_info()] + [1])
-    except Exception:
-        return os.cpu_count() or 1
+    """Host threads the oracle's mode products use (OpenMP over all cores; its
+    sweep is one sequential pass)."""
+    n = os.environ.get("OMP_NUM_THREADS")
+    return int(n) if n and n.isdigit() else (os.cpu_count() or 1)
 
 
 # --------------------------------------------------------------- clocks ----
@@ -90,6 +92,7 @@ class ClockSampler:
         self.proc = None
         self.lines = []
         self.active = False
+        self.label = "headline"
 
     def start(self):
         try:
@@ -105,9 +108,10 @@ class ClockSampler:
     def _read(self):
         for line in self.proc.stdout:
             if self.active:
-                self.lines.append(line.strip())
+                self.lines.append((self.label, line.strip()))
 
-    def mark(self, on: bool):
+    def mark(self, on: bool, label: str = "headline"):
+        self.label = label
         self.active = on
 
     def stop(self):
@@ -118,7 +122,10 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        rows = [l.split(", ") for l in self.lines if l.count(",") >= 8]
+        return self.summary("headline")
+
+    def summary(self, label: str):
+        rows = [l.split(", ") for lab, l in self.lines if lab == label and l.count(",") >= 8]
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
@@ -155,7 +162,8 @@ def run_reference(args, rank: int, world: int):
         "data": "synthetic", "config": config_block(),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": "one full CPU-oracle solve of the N=4, n=64 workload per "
-                                   "step (numpy/BLAS transforms, single-thread C sweep)"},
+                                   "step (C mode products over the host cores, "
+                                   "single-thread C sweep)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -471,6 +479,300 @@ def kernels_once(local: int, small_n: bool = False) -> int:
     return 0
 
 
+# ------------------------------------------------------------ workloads ----
+# Every synthetic configuration of the solver's benchmark suite, measured in
+# the default run beside the headline: FP64, mixed (FP64 residual) and mixed
+# with the tensor-core residual; error against the oracle (or the sampled
+# backward error where the oracle would take minutes); the phase split of one
+# solve with phase timing on; each phase's achieved rate against its roofline.
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "of measured (MEASURED_PEAKS.json hbm_gbs)"
+    except Exception:
+        return 6800.0, "of fallback (6.8 TB/s)"
+
+
+def phase_work(prec, desc, shape, E, iters):
+    """Work of each phase of one solve of one equation with E entries.
+
+    FP64 phases: flops, the method's count (Section 2.1, complex multiply-add =
+    8 flops: 8 n_j per entry and mode for a transform or residual pass,
+    4 sum_j (n_j - 1) + 11 for the sweep) and the count the kernels execute
+    (Gauss's three-multiplication product, 6 n_j, in the residual and in the
+    transform passes of even n_j >= 8).  FP32 and tensor-core phases: bytes of
+    the pass model, each of the plan's P passes reading and writing the tensor
+    once (complex64: 16 B per entry; +8 where a pass reads or writes
+    complex128; the correction's last back pass also reads X: +16); the sweep
+    16 B (complex64 in and out), or 32 B in FP64 for the entrywise division of
+    Remark 1; a tensor-core residual pass 48 B (X, R in and out)."""
+    P = desc["transform_passes"]
+    ns = [n for n in shape if n > 1]
+    meth = 8 * sum(ns) * E
+    exe_t = sum((6 * n if (n >= 8 and n % 2 == 0) else 8 * n) for n in ns) * E
+    sweep_f = (4 * sum(n - 1 for n in shape) + 11) * E
+    solves = 1 + iters
+    w = {}
+    if prec == "fp64":
+        w["forward"] = ("fp64", meth, exe_t)
+        w["back"] = ("fp64", meth, exe_t)
+        w["sweep"] = ("hbm", 32 * E, None) if desc["diag_sweep"] else ("fp64", sweep_f, sweep_f)
+        return w
+    emu = desc["residual_tc"] == 1
+    fwd_corr = 16 * P if emu else 16 * P + 8
+    w["forward"] = ("hbm", ((16 * P + 8) + fwd_corr * iters) * E, None)
+    w["back"] = ("hbm", ((16 * P + 8) + (16 * P + 24) * iters) * E, None)
+    w["sweep"] = ("hbm", 16 * E * solves, None)
+    if emu:
+        w["residual"] = ("hbm", 48 * desc["residual_passes"] * E * iters, None)
+    else:
+        w["residual"] = ("fp64", meth * iters, 6 * sum(ns) * E * iters)
+    return w
+
+
+def phase_roofline(prec, phases, descs, shapes, entries_per_eq, iters, hbm_gbs):
+    """Per-phase achieved rate and fraction of its roofline (summed over the
+    equations; `phases` in ms for one solve of each).  FP64 phases against the
+    FP64 pipe: `frac` from the executed flops, `frac_method_count` from the
+    method's own count (it exceeds 1 where three-multiplication products run);
+    the others against HBM with the pass model's bytes."""
+    tot = {}
+    for d, shp, E in zip(descs, shapes, entries_per_eq):
+        for ph, (kind, amt, exe) in phase_work(prec, d, shp, E, iters).items():
+            k, a, x = tot.get(ph, (kind, 0.0, 0.0))
+            tot[ph] = (kind, a + amt, x + (exe or 0.0))
+    out = {}
+    for ph, (kind, amt, exe) in tot.items():
+        ms = phases.get(ph, 0.0)
+        if ms <= 0 or amt <= 0:
+            continue
+        sec = ms * 1e-3
+        if kind == "fp64":
+            out[ph] = {"bound": "fp64 pipe", "achieved_tflops": exe / sec / 1e12,
+                       "frac": exe / sec / 1e12 / FP64_PEAK_TFLOPS,
+                       "frac_method_count": amt / sec / 1e12 / FP64_PEAK_TFLOPS}
+        else:
+            out[ph] = {"bound": "hbm", "achieved_gbs": amt / sec / 1e9,
+                       "frac": amt / sec / 1e9 / hbm_gbs}
+    return out
+
+
+def run_workloads(args, dev, sampler):
+    """The other configurations at N = 1 (see the module's workload list)."""
+    import torch
+    import oracle
+    from paper_2412_15840_gb300 import (Plan, from_device, solve_batched, to_device,
+                                        workspace_size_batched)
+    from paper_2412_15840_gb300.binding import schur as lib_schur
+    hbm_gbs, hbm_note = measured_peaks()
+    stream = torch.cuda.current_stream(dev)
+    res = {"peaks": {"fp64_tflops": FP64_PEAK_TFLOPS, "fp64_note": "derived: 152 SMs x 2 FMA/clk "
+                     "x 2 flops x 2070 MHz", "hbm_gbs": hbm_gbs, "hbm_note": hbm_note}}
+
+    def device_gaussian(shape_with_rhs, seed):
+        # unit-variance complex Gaussian drawn on the device (torch Philox,
+        # seeded): the 19^7 and batched right-hand sides are too large to draw
+        # on the host within the benchmark's time
+        g = torch.Generator(device=dev)
+        g.manual_seed(seed)
+        total = int(np.prod(shape_with_rhs, dtype=np.int64))
+        v = torch.randn(2 * total, generator=g, device=dev, dtype=torch.float64)
+        v.mul_(1.0 / np.sqrt(2.0))
+        return torch.view_as_complex(v.view(total, 2))
+
+    def measure(name, probs, Bs, precs, steps, warmup, check):
+        rec = {}
+        shapes = [p.shape for p in probs]
+        ents = [p.n_tot * p.nrhs for p in probs]
+        entries = sum(ents)
+        facs = [[lib_schur(a) if a.shape[0] > 1 else (np.eye(1, dtype=complex), a) for a in p.A]
+                for p in probs]
+        for prec in precs:
+            t0 = time.perf_counter()
+            plans = [Plan(Q=[f[0] for f in fa], T=[f[1] for f in fa], nrhs=p.nrhs, prec=prec,
+                          rtol=RTOL, max_refine=MAX_REFINE, device=dev.index)
+                     for p, fa in zip(probs, facs)]
+            setup = time.perf_counter() - t0
+            Xs = [torch.empty_like(b) for b in Bs]
+            if len(plans) == 1:
+                ws = plans[0].workspace()
+                step = lambda: plans[0].solve(Bs[0], Xs[0], workspace=ws, stream=stream)
+            else:
+                ws = torch.empty(max(256, workspace_size_batched(plans)), dtype=torch.uint8,
+                                 device=dev)
+                step = lambda: solve_batched(plans, Bs, Xs, ws, stream=stream)
+            for _ in range(warmup):
+                step()
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            sampler.mark(True, name)
+            e0.record(stream)
+            for _ in range(steps):
+                step()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            sampler.mark(False, name)
+            ms = e0.elapsed_time(e1) / steps
+            if len(plans) == 1:
+                _, info = plans[0].solve(Bs[0], Xs[0], workspace=ws, stream=stream, info=True)
+                infos = [info]
+            else:
+                infos = solve_batched(plans, Bs, Xs, ws, stream=stream, info=True)
+            r = {"ms_per_solve": ms, "entries_per_s": entries / (ms * 1e-3), "setup_s": setup,
+                 "status": sorted({i["status"] for i in infos}),
+                 "refine_iters_max": max(i["refine_iters"] for i in infos)}
+            if prec == "mixed_emu":
+                r["tensor_core_residual_equations"] = sum(bool(i["tensor_core_residual"])
+                                                          for i in infos)
+            r.update(check(prec, Xs))
+            # phase split: one more solve with phase timing on (a batch then runs
+            # its equations one after another instead of under the graph)
+            for pl in plans:
+                pl.set_timing(True)
+            if len(plans) == 1:
+                plans[0].solve(Bs[0], Xs[0], workspace=ws, stream=stream)
+            else:
+                solve_batched(plans, Bs, Xs, ws, stream=stream)
+            torch.cuda.synchronize(dev)
+            ph = {k: 0.0 for k in ("forward", "sweep", "back", "residual", "update", "total")}
+            for pl in plans:
+                t = pl.timing(reset=True)
+                pl.set_timing(False)
+                for k in ph:
+                    ph[k] += t["ms"][k]
+            r["phase_ms"] = ph
+            iters = r["refine_iters_max"] if prec != "fp64" else 0
+            descs = [pl.describe() for pl in plans]
+            r["phase_roofline"] = phase_roofline(prec, ph, descs, shapes, ents, iters, hbm_gbs)
+            d0 = descs[0]
+            r["plan"] = {k: d0[k] for k in ("transform_passes", "transform_tc_passes",
+                                            "residual_passes", "residual_tc", "diag_sweep",
+                                            "sweep_block", "sweep_threads", "sweep_ctas_per_sm",
+                                            "sweep_tile_levels", "sweep_far_split")} \
+                if len(plans) == 1 else {
+                    "transform_tc_passes": sum(d["transform_tc_passes"] for d in descs),
+                    "transform_passes": sum(d["transform_passes"] for d in descs),
+                    "diag_sweeps": sum(d["diag_sweep"] for d in descs)}
+            rec[prec] = r
+            del plans, Xs, ws
+            torch.cuda.empty_cache()
+        rec["clocks"] = sampler.summary(name)
+        rec["entries"] = entries
+        return rec
+
+    def oracle_check(probs, picks):
+        def check(prec, Xs):
+            errs = [oracle.rel_err(from_device(Xs[e], probs[e].B.shape),
+                                   oracle.solve(probs[e].A, probs[e].B)) for e in picks]
+            return {"rel_err_vs_oracle_max": max(errs), "oracle_checked_equations": len(picks)}
+        return check
+
+    def eta_check(p, Bdev):
+        def check(prec, Xs):
+            return {"sampled_backward_error": sampled_eta_dev(p.A, Bdev, Xs[0], p.shape, p.nrhs)}
+        return check
+
+    K = lambda k: max(1, min(args.steps, k))
+    W = max(1, min(args.warmup, 2))
+    precs = ("fp64", "mixed", "mixed_emu")
+    todo = [w.strip() for w in args.workloads.split(",") if w.strip()]
+
+    if "N3_n8" in todo:
+        p = si.cube_n8_N3()
+        Bs = [to_device(p.B, device=dev)]
+        Xo = oracle.solve(p.A, p.B)
+        chk = lambda prec, Xs: {"rel_err_vs_oracle": oracle.rel_err(
+            from_device(Xs[0], p.B.shape), Xo)}
+        res["N3_n8"] = {"config": "N=3, n_k=8 (512 entries), A=(randn+i randn)/sqrt(8)+3I, seed 0"}
+        res["N3_n8"].update(measure("N3_n8", [p], Bs, precs, K(20), W, chk))
+    if "N29_n2" in todo:
+        p = si.binary_N29()
+        Bd = to_device(p.B, device=dev)
+        res["N29_n2"] = {"config": "N=29, n_j=2 except singleton modes 5, 17 ([1.5]); 2x2 "
+                         "(randn+i randn)/sqrt(2)+2I; 2^27 entries; seed 0",
+                         "error_check": "backward error at 1000 sampled entries"}
+        res["N29_n2"].update(measure("N29_n2", [p], [Bd], precs, K(10), W, eta_check(p, Bd)))
+        del Bd
+    if "advdiff48" in todo:
+        p = si.advdiff_n48()
+        Bs = [to_device(p.B, device=dev)]
+        n = 48
+        h = 2 * np.pi / n
+        w = 2 * np.pi * np.arange(n) / n
+        lam = 0.01 * (2 * np.cos(w) - 2) / h ** 2 + 0.5 * (1j * np.sin(w)) / h + 1.0
+        Lam = lam[:, None, None] + lam[None, :, None] + lam[None, None, :]
+        Xf = np.fft.ifftn(np.fft.fftn(p.B, axes=(0, 1, 2)) / Lam[..., None], axes=(0, 1, 2))
+        chk = lambda prec, Xs: {"rel_err_vs_fft_closed_form": oracle.rel_err(
+            from_device(Xs[0], p.B.shape), Xf)}
+        res["advdiff48"] = {"config": "N=3, n=48 periodic advection-diffusion 0.01 D2 + 0.5 D1 "
+                            "+ I (h = 2 pi/48), 32 RHS, seed 0; normal operators (Remark 1)",
+                            "error_check": "FFT closed form (circulant operators)"}
+        res["advdiff48"].update(measure("advdiff48", [p], Bs, precs, K(20), W, chk))
+    if "batch512" in todo:
+        rng, shapes = si.batch_shapes(512, 0)
+        probs = [si.Problem(A=[si.gaussian_operator(rng, n, 3.0) for n in shp], B=None,
+                            name=f"batch{e}", meta={"shape": shp}) for e, shp in
+                 enumerate(shapes)]
+        Bs = [device_gaussian(p.meta["shape"] + (4,), 1000 + e) for e, p in enumerate(probs)]
+        for p in probs:      # B lives on the device; the host Problem carries the shape
+            p.B = np.lib.stride_tricks.as_strided(np.zeros(1, np.uint8), p.meta["shape"] + (4,),
+                                                  (0,) * 4)
+        big = [e for e, p in enumerate(probs) if max(p.shape) > 80][:6]
+        picks = sorted({int(np.argmax([p.n_tot for p in probs])),
+                        int(np.argmin([p.n_tot for p in probs]))} | set(big))
+        for e in picks:
+            probs[e].B = from_device(Bs[e], probs[e].B.shape)
+        res["batch512"] = {"config": "512 N=3 equations, n_k ~ U{16..96} (rng.integers, seed "
+                           "0), A=(randn+i randn)/sqrt(n)+3I, 4 RHS each, one batched call",
+                           "rhs": "drawn on the device (torch Philox, seeds 1000 + e)",
+                           "error_check": "oracle on the largest, the smallest and six "
+                                          "equations with a mode n > 80"}
+        res["batch512"].update(measure("batch512", probs, Bs, precs, K(3), 1,
+                                       oracle_check(probs, picks)))
+        del Bs
+    if "N7_n19" in todo:
+        rng = np.random.default_rng(0)
+        A = [si.gaussian_operator(rng, 19, 3.0) for _ in range(7)]
+        Bd = device_gaussian((19,) * 7 + (1,), 7)
+        # B lives on the device only; the host Problem carries the shape
+        q = si.Problem(A=A, B=np.lib.stride_tricks.as_strided(np.zeros(1, np.uint8),
+                                                               (19,) * 7 + (1,), (0,) * 8))
+
+        def chk(prec, Xs):
+            return {"sampled_backward_error": sampled_eta_dev(A, Bd, Xs[0], (19,) * 7, 1)}
+        res["N7_n19"] = {"config": "N=7, n=19 (893,871,739 entries), A=(randn+i randn)/sqrt(19)"
+                         "+3I (seed 0); B drawn on the device (torch Philox, seed 7)",
+                         "error_check": "backward error at 1000 sampled entries"}
+        res["N7_n19"].update(measure("N7_n19", [q], [Bd], precs, K(3), 1, chk))
+        del Bd
+    torch.cuda.empty_cache()
+    return res
+
+
+def sampled_eta_dev(A, B_dev, X_dev, shape, nrhs, count=1000, seed=11):
+    """sampled_eta with B on the device (gathered at the sampled entries)."""
+    import torch
+    rng = np.random.default_rng(seed)
+    N = len(shape)
+    S = np.cumprod((1,) + tuple(shape[:-1]), dtype=np.int64)
+    ntot = int(np.prod(shape, dtype=np.int64))
+    ii = np.stack([rng.integers(0, shape[j], size=count) for j in range(N)], axis=1)
+    lin = (ii * S).sum(axis=1) + rng.integers(0, nrhs, size=count) * ntot
+    acc = np.zeros(count, dtype=np.complex128)
+    for j in range(N):
+        idx = lin[:, None] + (np.arange(shape[j])[None, :] - ii[:, j:j + 1]) * S[j]
+        xs = X_dev[torch.as_tensor(idx.reshape(-1), device=X_dev.device)].cpu().numpy()
+        acc += np.einsum("ck,ck->c", A[j][ii[:, j], :], xs.reshape(count, shape[j]))
+    b = B_dev[torch.as_tensor(lin, device=B_dev.device)].cpu().numpy()
+    r = b - acc
+    an = sum(float(np.abs(a).sum(axis=1).max()) for a in A)
+    return float(np.abs(r).max()) / (an * float(X_dev.abs().max().item()) +
+                                     float(B_dev.abs().max().item()))
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -660,7 +962,7 @@ def main():
     barrier()
     ms_e2e = max_over_ranks(t_start.elapsed_time(t_end) / args.steps)
     e2e_matches = bool(torch.equal(Xh[(args.steps - 1) % 2], X_ref_flat))
-    clocks = sampler.stop()
+    clocks = sampler.summary("headline")
 
     value = world * entries / (ms_mixed * 1e-3)
     value_fp64 = world * entries / (ms_fp64 * 1e-3)
@@ -719,6 +1021,27 @@ def main():
                                     for k, v in phases_e["ms"].items()}},
     }
 
+    hbm_gbs, _ = measured_peaks()
+    line["phase_roofline"] = {
+        "mixed": phase_roofline("mixed", line["phases_ms_per_solve"]["mixed"], [mixed.describe()],
+                                [SHAPE], [entries], info_m["refine_iters"], hbm_gbs),
+        "fp64": phase_roofline("fp64", line["phases_ms_per_solve"]["fp64"], [fp64.describe()],
+                               [SHAPE], [entries], 0, hbm_gbs),
+        "mixed_emu": phase_roofline("mixed_emu", line["mixed_emu"]["phases_ms_per_solve"],
+                                    [emu.describe()], [SHAPE], [entries], info_e["refine_iters"],
+                                    hbm_gbs)}
+    line["plans"] = {"mixed": mixed.describe(), "fp64": fp64.describe(),
+                     "mixed_emu": emu.describe()}
+    for d in line["plans"].values():
+        d["sweep_block"] = list(d["sweep_block"])
+    del X_mixed, X64, Xe, Bd, Xd, B, X
+    torch.cuda.empty_cache()
+    if world == 1 and args.workloads not in ("", "none"):
+        line["workloads"] = run_workloads(args, dev, sampler)
+        line["workloads"]["N4_n64"] = "this line's headline (value, fp64, mixed_emu, " \
+                                      "phases_ms_per_solve, phase_roofline)"
+    sampler.stop()
+
     if rank == 0 and not args.no_oracle:
         import oracle
         t0 = time.perf_counter()
@@ -730,7 +1053,8 @@ def main():
         line["cpu_baseline"] = {
             "value": entries / dt, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
             "sample": "one full CPU-oracle solve of this rank-0 N=4, n=64 equation "
-                      "(numpy/BLAS transforms, single-thread C sweep); " f"{dt:.1f} s"}
+                      "(C mode products over the host cores, single-thread C sweep); "
+                      f"{dt:.1f} s"}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

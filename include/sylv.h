@@ -325,6 +325,31 @@ sylv_status sylv_plan_autotune(sylv_plan_t plan, void *T_dev, void *workspace,
                                size_t workspace_bytes, void *stream, int32_t *block_out,
                                float *best_ms);
 
+/*
+ * sylv_plan_describe -- the launch structure the plan chose (host-only, no
+ * device work): how Algorithm 3's phases map onto passes and tiles on this
+ * GPU.  Useful to relate a measured phase time to its pass-model traffic
+ * and to report the settings that sylv_plan_autotune picked.
+ */
+typedef struct {
+    int32_t transform_passes;   /* passes of one forward (= one back) transform in the
+                                   working precision (fused groups of adjacent modes) */
+    int32_t transform_tc_passes;/* of which on the tensor cores (tcgen05)              */
+    int32_t residual_passes;    /* passes of one residual (mixed precisions)           */
+    int32_t residual_tc;        /* 1: the residual runs on the tensor cores            */
+    int32_t diag_sweep;         /* 1: the sweep is the entrywise division of Remark 1  */
+    int32_t sweep_threads;      /* threads per CTA of the tiled sweep                  */
+    int32_t sweep_ctas_per_sm;  /* resident CTAs per SM of its persistent grid         */
+    int32_t sweep_grid;         /* CTAs of its persistent grid                         */
+    int64_t sweep_tiles;        /* tiles (right-hand sides included)                   */
+    int32_t sweep_tile_entries; /* entries of a full tile                              */
+    int32_t sweep_tile_levels;  /* tile levels sum_j (blocks_j - 1) + 1                */
+    int32_t sweep_inv_table;    /* 1: FP64 reciprocals read from the plan's table      */
+    int32_t sweep_far_split;    /* 1: far strips applied ahead of the full wait        */
+    int32_t sweep_block[64];    /* tile extent along each input mode (first N used)    */
+} sylv_plan_desc;
+sylv_status sylv_plan_describe(sylv_plan_t plan, sylv_plan_desc *out);
+
 /* The plan's Schur factors of input mode j (host copies; Q is the identity
  * 1x1 for a singleton).  Q_out and T_out hold n_j*n_j complex128 each. */
 sylv_status sylv_plan_factors(sylv_plan_t plan, int j, double *Q_out, double *T_out);

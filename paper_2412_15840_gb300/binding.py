@@ -35,7 +35,8 @@ EXPORTED = ("sylv_plan_create", "sylv_plan_destroy", "sylv_workspace_size", "syl
             "sylv_back", "sylv_residual", "sylv_plan_factors", "sylv_plan_set_timing",
             "sylv_plan_timing", "sylv_schur", "sylv_status_string", "sylv_version",
             "sylv_sweep_static", "sylv_plan_autotune", "sylv_evolve_workspace_size",
-            "sylv_evolve", "sylv_expm", "sylv_schur_real", "sylv_plan_create_real")
+            "sylv_evolve", "sylv_expm", "sylv_schur_real", "sylv_plan_create_real",
+            "sylv_plan_describe")
 
 
 class SylvError(RuntimeError):
@@ -62,6 +63,16 @@ class Info(ctypes.Structure):
 class Timing(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 8), ("launches", ctypes.c_int64 * 8),
                 ("solves", ctypes.c_int64)]
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [("transform_passes", ctypes.c_int32), ("transform_tc_passes", ctypes.c_int32),
+                ("residual_passes", ctypes.c_int32), ("residual_tc", ctypes.c_int32),
+                ("diag_sweep", ctypes.c_int32), ("sweep_threads", ctypes.c_int32),
+                ("sweep_ctas_per_sm", ctypes.c_int32), ("sweep_grid", ctypes.c_int32),
+                ("sweep_tiles", ctypes.c_int64), ("sweep_tile_entries", ctypes.c_int32),
+                ("sweep_tile_levels", ctypes.c_int32), ("sweep_inv_table", ctypes.c_int32),
+                ("sweep_far_split", ctypes.c_int32), ("sweep_block", ctypes.c_int32 * 64)]
 
 
 class Tuning(ctypes.Structure):
@@ -121,6 +132,8 @@ def _lib():
         L.sylv_residual.argtypes = [vp, vp, vp, vp, vp]
         L.sylv_plan_factors.restype = st
         L.sylv_plan_factors.argtypes = [vp, ctypes.c_int, vp, vp]
+        L.sylv_plan_describe.restype = st
+        L.sylv_plan_describe.argtypes = [vp, ctypes.POINTER(Desc)]
         L.sylv_plan_set_timing.restype = st
         L.sylv_plan_set_timing.argtypes = [vp, ctypes.c_int]
         L.sylv_plan_timing.restype = st
@@ -459,6 +472,14 @@ class Plan:
         _check(_lib().sylv_plan_factors(self._h, j, Q.ctypes.data, T.ctypes.data),
                "sylv_plan_factors")
         return Q, T
+
+    def describe(self) -> dict:
+        """sylv_plan_describe: passes, tiles and launch shapes the plan chose."""
+        d = Desc()
+        _check(_lib().sylv_plan_describe(self._h, ctypes.byref(d)), "sylv_plan_describe")
+        out = {k: getattr(d, k) for k, _ in Desc._fields_ if k != "sweep_block"}
+        out["sweep_block"] = tuple(int(d.sweep_block[j]) for j in range(self.N))
+        return out
 
     def set_timing(self, enable: bool = True):
         _check(_lib().sylv_plan_set_timing(self._h, int(bool(enable))), "sylv_plan_set_timing")

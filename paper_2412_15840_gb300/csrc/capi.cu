@@ -97,6 +97,9 @@ struct SweepConfig {
     int threads = 256, grid = 1, per_sm = 1;
     size_t smem = 0;
     void *dbuf = nullptr;
+    // device copy of `a` with the plan's factor pointers filled in (Y, cnt and
+    // flags are per call): the batched sweep reads each equation's from here
+    const SweepArgs *dargs = nullptr;
 };
 
 struct DeviceGuard {
@@ -448,8 +451,21 @@ int64_t tiles_for(const sylv_plan_s &p, const int *b) {
     return ts * p.nrhs;
 }
 
+// The plan's factor pointers of the sweep in its working precision.
+void fill_sweep_ptrs(const sylv_plan_s &p, SweepArgs &a, bool fp64) {
+    for (int j = 0; j < p.Nm; ++j) {
+        a.T[j] = fp64 ? p.T64[j] : p.T32[j];
+        a.d[j] = p.d64[j];
+        a.Tr[j] = fp64 ? p.Tr64[j] : p.Tr32[j];
+        a.Vp[j] = p.has_pairs[j] ? (fp64 ? p.V64[j] : p.V32[j]) : nullptr;
+    }
+    a.den_scale = p.den_scale;
+    a.inv_tab = p.inv_tab;
+}
+
 // Host tables of one sweep configuration (tile extents b, `threads` per CTA),
-// uploaded into a device buffer of its own.
+// uploaded into a device buffer of its own, followed by a device copy of the
+// configuration's arguments.
 sylv_status build_sweep(const sylv_plan_s &p, const int *b, int threads, SweepConfig &cfg,
                         int ctas_per_sm = 0) {
     SweepArgs &a = cfg.a;
@@ -577,7 +593,8 @@ sylv_status build_sweep(const sylv_plan_s &p, const int *b, int threads, SweepCo
     size_t o_lev = align256(o_sched + sched.size() * 4);
     size_t o_se = align256(o_lev + lev.size() * 4);
     size_t o_coord = align256(o_se + sched_e.size() * 4);
-    size_t total = align256(o_coord + coord.size() * 8);
+    size_t o_args = align256(o_coord + coord.size() * 8);
+    size_t total = align256(o_args + sizeof(SweepArgs));
     std::vector<unsigned char> host(total, 0);
     std::memcpy(host.data() + o_order, order.data(), order.size() * 4);
     std::memcpy(host.data() + o_sched, sched.data(), sched.size() * 4);
@@ -597,6 +614,7 @@ sylv_status build_sweep(const sylv_plan_s &p, const int *b, int threads, SweepCo
     a.lev_start = (const int *)(base + o_lev);
     a.sched_e = (const int *)(base + o_se);
     a.coord = (const unsigned long long *)(base + o_coord);
+    cfg.dargs = (const SweepArgs *)(base + o_args);
 
     // persistent grid: every SM holds as many tiles as fit, or the requested
     // number (fewer CTAs per SM shorten each tile's latency on the dependency
@@ -609,6 +627,10 @@ sylv_status build_sweep(const sylv_plan_s &p, const int *b, int threads, SweepCo
     // far strips ahead of the full dependency wait pay where the sweep is bound by
     // its dependency chain: at most two tiles per level for each resident CTA
     a.far_split = a.ntiles <= (int64_t)2 * cfg.grid * (maxlev + 1) ? 1 : 0;
+    SweepArgs full = a;
+    fill_sweep_ptrs(p, full, p.fp64());
+    if (cudaMemcpy(base + o_args, &full, sizeof(full), cudaMemcpyHostToDevice) != cudaSuccess)
+        return SYLV_ERR_CUDA;
     return SYLV_OK;
 }
 
@@ -812,14 +834,7 @@ cudaError_t run_sweep_cfg(Ctx &c, const SweepConfig &cfg, void *Y, bool fp64) {
     sylv_plan_s *p = c.p;
     SweepArgs a = cfg.a;
     a.Y = Y;
-    for (int j = 0; j < p->Nm; ++j) {
-        a.T[j] = fp64 ? p->T64[j] : p->T32[j];
-        a.d[j] = p->d64[j];
-        a.Tr[j] = fp64 ? p->Tr64[j] : p->Tr32[j];
-        a.Vp[j] = p->has_pairs[j] ? (fp64 ? p->V64[j] : p->V32[j]) : nullptr;
-    }
-    a.den_scale = p->den_scale;
-    a.inv_tab = p->inv_tab;
+    fill_sweep_ptrs(*p, a, fp64);
     a.cnt = c.cnt;
     a.flags = c.flags;
     cudaError_t e = launch_sweep_init(a, c.st);
@@ -870,88 +885,111 @@ sylv_status fill_info(sylv_plan_s *p, DevFlags *flags, cudaStream_t st, sylv_inf
     return s;
 }
 
-sylv_status solve_impl(sylv_plan_s *p, const void *B, void *X, void *ws, cudaStream_t st,
-                       int &launches) {
-    Ctx c{p, st, reinterpret_cast<DevFlags *>(ws),
-          reinterpret_cast<int *>((char *)ws + p->off_cnt)};
+// A solve is a launch sequence with sweeps between its segments: segment 0
+// (init, forward), then for FP64 one sweep and segment 1 (back); for the mixed
+// path a sweep before each of segments 1 .. max_refine + 1 (back, refinement
+// decision, and -- except in the last -- residual and forward of the next
+// correction).  Batched solves interleave equations segment by segment.
+int solve_sweeps(const sylv_plan_s *p) { return p->fp64() ? 1 : 1 + p->max_refine; }
+
+// the tensor the sweep after segment `seg` works on
+void *sweep_tensor(const sylv_plan_s *p, void *X, void *ws) {
+    return p->fp64() ? X : (char *)ws + p->off_W;
+}
+
+Ctx make_ctx(sylv_plan_s *p, void *ws, cudaStream_t st) {
+    return Ctx{p, st, reinterpret_cast<DevFlags *>(ws),
+               reinterpret_cast<int *>((char *)ws + p->off_cnt)};
+}
+
+sylv_status solve_segment(Ctx &c, const void *B, void *X, void *ws, int seg) {
+    sylv_plan_s *p = c.p;
+    cudaStream_t st = c.st;
     cudaError_t e;
     const int KH = p->khi(), KL = p->klo();
-    const bool timing = p->timing;
-    cudaEvent_t t0 = nullptr;
-    if (timing) { t0 = take_event(p); cudaEventRecord(t0, st); }
-    if ((e = launch_solve_init(c.flags, st)) != cudaSuccess) return SYLV_ERR_CUDA;
-    count(c);
     if (p->fp64()) {
-        phase_begin(c, SYLV_PH_FORWARD);
-        if (p->Nm == 0) {
-            if (B != X && cudaMemcpyAsync(X, B, (size_t)(p->ntot * p->nrhs) * p->ehi(),
-                                          cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        if (seg == 0) {
+            if ((e = launch_solve_init(c.flags, st)) != cudaSuccess) return SYLV_ERR_CUDA;
+            count(c);
+            phase_begin(c, SYLV_PH_FORWARD);
+            if (p->Nm == 0) {
+                if (B != X && cudaMemcpyAsync(X, B, (size_t)(p->ntot * p->nrhs) * p->ehi(),
+                                              cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+                    return SYLV_ERR_CUDA;
+            } else if ((e = run_groups(c, p->tgroups, true, 0, B, KH, X, KH, X,
+                                       KH, EPI_STORE, nullptr)) != cudaSuccess)
                 return SYLV_ERR_CUDA;
-        } else if ((e = run_groups(c, p->tgroups, true, 0, B, KH, X, KH, X,
-                                   KH, EPI_STORE, nullptr)) != cudaSuccess)
-            return SYLV_ERR_CUDA;
-        phase_end(c);
-        phase_begin(c, SYLV_PH_SWEEP);
-        if ((e = run_sweep(c, X, true)) != cudaSuccess) return SYLV_ERR_CUDA;
-        phase_end(c);
-        phase_begin(c, SYLV_PH_BACK);
-        if (p->Nm > 0 && (e = run_groups(c, p->tgroups, true, 1, X, KH, X, KH, X,
-                                         KH, EPI_STORE, nullptr)) != cudaSuccess)
-            return SYLV_ERR_CUDA;
-        phase_end(c);
-    } else {
-        void *W = (char *)ws + p->off_W;
-        void *R = (char *)ws + p->off_R;
-        const int *done = &c.flags->done;
-        // initial low-precision solve X_0
+            phase_end(c);
+        } else {
+            phase_begin(c, SYLV_PH_BACK);
+            if (p->Nm > 0 && (e = run_groups(c, p->tgroups, true, 1, X, KH, X, KH, X,
+                                             KH, EPI_STORE, nullptr)) != cudaSuccess)
+                return SYLV_ERR_CUDA;
+            phase_end(c);
+        }
+        return SYLV_OK;
+    }
+    void *W = (char *)ws + p->off_W;
+    void *R = (char *)ws + p->off_R;
+    const int *done = &c.flags->done;
+    if (seg == 0) {
+        // initial low-precision solve X_0: forward of B
+        if ((e = launch_solve_init(c.flags, st)) != cudaSuccess) return SYLV_ERR_CUDA;
+        count(c);
         phase_begin(c, SYLV_PH_FORWARD);
         if ((e = run_groups(c, p->tgroups, false, 0, B, KH, W, KL, W, KL,
                             EPI_STORE, nullptr)) != cudaSuccess)
             return SYLV_ERR_CUDA;
         phase_end(c);
+        return SYLV_OK;
+    }
+    // back transform of the solve before this segment: X_0 = Y (seg 1) or X += D
+    phase_begin(c, SYLV_PH_BACK);
+    if (seg == 1 ? run_groups(c, p->tgroups, false, 1, W, KL, W, KL, X, KH,
+                              EPI_STORE_NORM, nullptr) != cudaSuccess
+                 : run_groups(c, p->tgroups, false, 1, W, KL, W, KL, X, KH,
+                              EPI_ACCUM, done) != cudaSuccess)
+        return SYLV_ERR_CUDA;
+    phase_end(c);
+    phase_begin(c, SYLV_PH_UPDATE);
+    if (launch_refine_decide(c.flags, (float)p->rtol, seg - 1, p->max_refine, c.st) != cudaSuccess)
+        return SYLV_ERR_CUDA;
+    count(c);
+    phase_end(c);
+    if (seg > p->max_refine) return SYLV_OK;
+    // correction `seg`: residual and forward transform of it
+    phase_begin(c, SYLV_PH_RESIDUAL);
+    if (p->oz) {
+        // tensor-core residual: complex64 R straight into W
+        if (run_residual_oz(c, B, X, R, W, done) != cudaSuccess) return SYLV_ERR_CUDA;
+    } else if (run_residual(c, B, X, R, done) != cudaSuccess) {
+        return SYLV_ERR_CUDA;
+    }
+    phase_end(c);
+    phase_begin(c, SYLV_PH_FORWARD);
+    if (p->oz ? run_groups(c, p->tgroups, false, 0, W, KL, W, KL, W, KL,
+                           EPI_STORE, done) != cudaSuccess
+              : run_groups(c, p->tgroups, false, 0, R, KH, W, KL, W, KL,
+                           EPI_STORE, done) != cudaSuccess)
+        return SYLV_ERR_CUDA;
+    phase_end(c);
+    return SYLV_OK;
+}
+
+sylv_status solve_impl(sylv_plan_s *p, const void *B, void *X, void *ws, cudaStream_t st,
+                       int &launches) {
+    Ctx c = make_ctx(p, ws, st);
+    const bool timing = p->timing;
+    cudaEvent_t t0 = nullptr;
+    if (timing) { t0 = take_event(p); cudaEventRecord(t0, st); }
+    const int nsw = solve_sweeps(p);
+    for (int seg = 0; seg <= nsw; ++seg) {
+        sylv_status s = solve_segment(c, B, X, ws, seg);
+        if (s != SYLV_OK) return s;
+        if (seg == nsw) break;
         phase_begin(c, SYLV_PH_SWEEP);
-        if ((e = run_sweep(c, W, false)) != cudaSuccess) return SYLV_ERR_CUDA;
+        if (run_sweep(c, sweep_tensor(p, X, ws), p->fp64()) != cudaSuccess) return SYLV_ERR_CUDA;
         phase_end(c);
-        phase_begin(c, SYLV_PH_BACK);
-        if ((e = run_groups(c, p->tgroups, false, 1, W, KL, W, KL, X, KH,
-                            EPI_STORE_NORM, nullptr)) != cudaSuccess)
-            return SYLV_ERR_CUDA;
-        phase_end(c);
-        phase_begin(c, SYLV_PH_UPDATE);
-        if (launch_refine_decide(c.flags, (float)p->rtol, 0, p->max_refine, c.st) != cudaSuccess)
-            return SYLV_ERR_CUDA;
-        count(c);
-        phase_end(c);
-        for (int it = 1; it <= p->max_refine; ++it) {
-            phase_begin(c, SYLV_PH_RESIDUAL);
-            if (p->oz) {
-                // tensor-core residual: complex64 R straight into W
-                if (run_residual_oz(c, B, X, R, W, done) != cudaSuccess) return SYLV_ERR_CUDA;
-            } else if (run_residual(c, B, X, R, done) != cudaSuccess) {
-                return SYLV_ERR_CUDA;
-            }
-            phase_end(c);
-            phase_begin(c, SYLV_PH_FORWARD);
-            if (p->oz ? run_groups(c, p->tgroups, false, 0, W, KL, W, KL, W, KL,
-                                   EPI_STORE, done) != cudaSuccess
-                      : run_groups(c, p->tgroups, false, 0, R, KH, W, KL, W, KL,
-                                   EPI_STORE, done) != cudaSuccess)
-                return SYLV_ERR_CUDA;
-            phase_end(c);
-            phase_begin(c, SYLV_PH_SWEEP);
-            if (run_sweep(c, W, false) != cudaSuccess) return SYLV_ERR_CUDA;
-            phase_end(c);
-            phase_begin(c, SYLV_PH_BACK);
-            if (run_groups(c, p->tgroups, false, 1, W, KL, W, KL, X, KH,
-                           EPI_ACCUM, done) != cudaSuccess)
-                return SYLV_ERR_CUDA;
-            phase_end(c);
-            phase_begin(c, SYLV_PH_UPDATE);
-            if (launch_refine_decide(c.flags, (float)p->rtol, it, p->max_refine, c.st) != cudaSuccess)
-                return SYLV_ERR_CUDA;
-            count(c);
-            phase_end(c);
-        }
     }
     if (timing) {
         cudaEvent_t t1 = take_event(p);
@@ -1002,6 +1040,62 @@ void batch_forget(const void *p) {
     }
 }
 
+// One segment's sweeps of the equations `eqs` (tiled sweeps): grouped by
+// kernel template and block size, each group in chunks of at most SWB_MAX
+// equations, one persistent launch per chunk (k_sweep_batch) on `st`.  Larger
+// equations first, so that the CTAs' work-weighted starts spread over them.
+cudaError_t run_sweep_batched(const sylv_plan_t *plans, void *const *X, void *ws,
+                              const std::vector<size_t> &off, const std::vector<int> &eqs,
+                              cudaStream_t st, std::vector<Ctx> &ctx) {
+    std::vector<int> order(eqs);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        const sylv_plan_s *a = plans[x], *b = plans[y];
+        const int ka = (a->fp64() ? 4 : 0) + (a->real ? 2 : 0), kb = (b->fp64() ? 4 : 0) + (b->real ? 2 : 0);
+        if (ka != kb) return ka < kb;
+        if (a->sweep.threads != b->sweep.threads) return a->sweep.threads < b->sweep.threads;
+        return a->sweep.a.ntiles > b->sweep.a.ntiles;
+    });
+    auto same = [&](int x, int y) {
+        const sylv_plan_s *a = plans[x], *b = plans[y];
+        return a->fp64() == b->fp64() && a->real == b->real && a->sweep.threads == b->sweep.threads;
+    };
+    std::unique_ptr<SweepBatch> bt(new (std::nothrow) SweepBatch);
+    if (!bt) return cudaErrorMemoryAllocation;
+    const int num_sms = plans[order[0]]->num_sms;
+    for (size_t i = 0; i < order.size();) {
+        size_t j = i;
+        while (j < order.size() && j - i < (size_t)SWB_MAX && same(order[i], order[j])) ++j;
+        std::memset(bt.get(), 0, sizeof(SweepBatch));
+        bt->neq = (int)(j - i);
+        bt->far_split = bt->neq == 1 ? 1 : 0;
+        size_t smem = 0;
+        long long cum = 0;
+        for (size_t q = i; q < j; ++q) {
+            const int e = order[q];
+            sylv_plan_s *p = plans[e];
+            const int k = (int)(q - i);
+            bt->sa[k] = p->sweep.dargs;
+            bt->Y[k] = sweep_tensor(p, X[e], (char *)ws + off[(size_t)e]);
+            bt->cnt[k] = reinterpret_cast<int *>((char *)ws + off[(size_t)e] + p->off_cnt);
+            bt->flags[k] = reinterpret_cast<DevFlags *>((char *)ws + off[(size_t)e]);
+            bt->cum[k] = cum;
+            cum += p->sweep.a.ntiles;
+            smem = std::max(smem, p->sweep.smem);
+            ctx[(size_t)e].launches += 2;
+        }
+        bt->cum[bt->neq] = cum;
+        const sylv_plan_s *p0 = plans[order[i]];
+        const int threads = p0->sweep.threads;
+        int per = sweep_batch_blocks_per_sm(p0->fp64(), threads, smem, p0->real ? 1 : 0);
+        if (per < 1) per = 1;
+        const int grid = (int)std::max<long long>(1, std::min<long long>((long long)num_sms * per, cum));
+        cudaError_t e = launch_sweep_batch(p0->fp64(), p0->real ? 1 : 0, *bt, grid, threads, smem, st);
+        if (e != cudaSuccess) return e;
+        i = j;
+    }
+    return cudaSuccess;
+}
+
 sylv_status batch_graph_launch(int count, const sylv_plan_t *plans, const void *const *B,
                                void *const *X, void *ws, cudaStream_t user,
                                std::vector<int> &launches) {
@@ -1034,16 +1128,46 @@ sylv_status batch_graph_launch(int count, const sylv_plan_t *plans, const void *
     }
     const int S = std::min(count, BATCH_STREAMS);
     cudaStream_t cs = ds.s[0];
+    std::vector<size_t> off((size_t)count, 0);
+    for (int e = 1; e < count; ++e) off[(size_t)e] = off[(size_t)e - 1] + align256(plans[e - 1]->ws_bytes);
+    std::vector<Ctx> ctx;
+    ctx.reserve((size_t)count);
+    int maxsw = 0;
+    for (int e = 0; e < count; ++e) {
+        ctx.push_back(make_ctx(plans[e], (char *)ws + off[(size_t)e], ds.s[e % S]));
+        maxsw = std::max(maxsw, solve_sweeps(plans[e]));
+    }
     if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
         return SYLV_ERR_CUDA;
     bool ok = cudaEventRecord(ds.fork, cs) == cudaSuccess;
     for (int k = 1; ok && k < S; ++k) ok = cudaStreamWaitEvent(ds.s[k], ds.fork, 0) == cudaSuccess;
-    size_t off = 0;
-    for (int e = 0; ok && e < count; ++e) {
-        ok = solve_impl(plans[e], B[e], X[e], (char *)ws + off, ds.s[e % S],
-                        launches[(size_t)e]) == SYLV_OK;
-        off += align256(plans[e]->ws_bytes);
+    // segment by segment: every equation's launches up to its next sweep on its
+    // stream; then one batched sweep over the equations with tiled sweeps (the
+    // entrywise-division sweeps of Remark 1 stay on their own streams)
+    for (int seg = 0; ok && seg <= maxsw; ++seg) {
+        std::vector<int> tiled;
+        for (int e = 0; ok && e < count; ++e) {
+            sylv_plan_s *p = plans[e];
+            const int nsw = solve_sweeps(p);
+            if (seg > nsw) continue;
+            ok = solve_segment(ctx[(size_t)e], B[e], X[e], (char *)ws + off[(size_t)e], seg) ==
+                 SYLV_OK;
+            if (!ok || seg == nsw) continue;
+            if (p->diag_sweep || p->Nm == 0)
+                ok = run_sweep(ctx[(size_t)e], sweep_tensor(p, X[e], (char *)ws + off[(size_t)e]),
+                               p->fp64()) == cudaSuccess;
+            else
+                tiled.push_back(e);
+        }
+        if (!ok || tiled.empty()) continue;
+        for (int k = 1; ok && k < S; ++k)
+            ok = cudaEventRecord(ds.join[k], ds.s[k]) == cudaSuccess &&
+                 cudaStreamWaitEvent(cs, ds.join[k], 0) == cudaSuccess;
+        if (ok) ok = run_sweep_batched(plans, X, ws, off, tiled, cs, ctx) == cudaSuccess;
+        if (ok) ok = cudaEventRecord(ds.fork, cs) == cudaSuccess;
+        for (int k = 1; ok && k < S; ++k) ok = cudaStreamWaitEvent(ds.s[k], ds.fork, 0) == cudaSuccess;
     }
+    for (int e = 0; e < count; ++e) launches[(size_t)e] = ctx[(size_t)e].launches;
     for (int k = 1; ok && k < S; ++k)
         ok = cudaEventRecord(ds.join[k], ds.s[k]) == cudaSuccess &&
              cudaStreamWaitEvent(cs, ds.join[k], 0) == cudaSuccess;
@@ -2010,6 +2134,32 @@ sylv_status sylv_plan_factors(sylv_plan_t p, int j, double *Qo, double *To) {
         Qo[2 * k] = Q[k].real(); Qo[2 * k + 1] = Q[k].imag();
         To[2 * k] = T[k].real(); To[2 * k + 1] = T[k].imag();
     }
+    return SYLV_OK;
+}
+
+sylv_status sylv_plan_describe(sylv_plan_t p, sylv_plan_desc *out) {
+    if (!p || !out) return SYLV_ERR_INVALID_ARG;
+    std::memset(out, 0, sizeof(*out));
+    out->transform_passes = p->Nm > 0 ? (int32_t)p->tgroups.size() : 0;
+    for (const auto &g : p->tgroups) out->transform_tc_passes += g.tc ? 1 : 0;
+    if (!p->fp64()) {
+        out->residual_tc = p->oz ? 1 : 0;
+        out->residual_passes = p->oz ? (int32_t)p->ozpasses.size() : (int32_t)p->rgroups.size();
+    }
+    out->diag_sweep = p->diag_sweep ? 1 : 0;
+    const SweepArgs &a = p->sweep.a;
+    out->sweep_threads = p->sweep.threads;
+    out->sweep_ctas_per_sm = p->sweep.per_sm;
+    out->sweep_grid = p->sweep.grid;
+    out->sweep_tiles = a.ntiles;
+    out->sweep_tile_entries = a.Pt;
+    int lev = 1;
+    for (int j = 0; j < p->Nm; ++j) lev += a.Bc[j] - 1;
+    out->sweep_tile_levels = lev;
+    out->sweep_inv_table = p->inv_tab ? 1 : 0;
+    out->sweep_far_split = a.far_split;
+    for (int j = 0, q = 0; j < p->N_in && j < 64; ++j)
+        out->sweep_block[j] = (q < p->Nm && p->orig[q] == j) ? a.b[q++] : 1;
     return SYLV_OK;
 }
 

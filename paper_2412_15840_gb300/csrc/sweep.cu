@@ -149,8 +149,11 @@ __device__ __forceinline__ void rotate_pairs(const SweepArgs &a, C2 *tile_s, con
     }
 }
 
+// Every tile of one equation: take tickets from the equation's own counter
+// (a.flags->ticket) until they run out.  far_ok = 0 turns the far/near strip
+// split off (a batch of equations keeps the GPU busy without it).
 template <typename real, bool RL>
-__global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const __grid_constant__ SweepArgs a) {
+__device__ __forceinline__ void sweep_drain(const SweepArgs &a, const int far_ok) {
     using C2 = typename C2T<real>::type;
     using YT = typename std::conditional<RL, real, C2>::type;   // element of C and Y
     using Inv = typename InvT<real>::type;
@@ -445,7 +448,7 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
         // far strips can be applied while the successors themselves still run.
         // Only when the sweep is latency-bound (few tiles per level for the
         // resident CTAs): otherwise the extra staging passes cost throughput.
-        const bool split = a.far_split && s_hasfar;
+        const bool split = far_ok && a.far_split && s_hasfar;
         if (split) {
         if (threadIdx.x == 0) {
             volatile int *err = &a.flags->err;
@@ -657,6 +660,88 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const 
     }
 }
 
+template <typename real, bool RL>
+__global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep(const __grid_constant__ SweepArgs a) {
+    sweep_drain<real, RL>(a, 1);
+}
+
+// Batched sweep (many independent equations, one persistent launch): every
+// equation keeps its own ticket counter, level-ordered tile list and tile
+// counters, so a CTA waits only on tiles of the same equation with smaller
+// tickets, which running CTAs hold -- the single-equation argument, whatever
+// order the CTAs visit the equations in.  A CTA starts at the equation that
+// its share of the summed tile count falls in, drains it, and moves on to the
+// first equation after it (cyclically) that still has tickets left; an
+// equation's arguments are staged in shared memory while the CTA works on it.
+template <typename real, bool RL>
+__global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_sweep_batch(const __grid_constant__ SweepBatch bt) {
+    __shared__ __align__(16) SweepArgs sa;
+    __shared__ int s_next;
+    const int neq = bt.neq;
+    const long long target = (long long)blockIdx.x * bt.cum[neq] / gridDim.x;
+    int lo = 0, hi = neq - 1;           // the equation whose tile range holds `target`
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (bt.cum[mid] <= target) lo = mid;
+        else hi = mid - 1;
+    }
+    constexpr int WORDS = (int)(sizeof(SweepArgs) / sizeof(int));
+    int cur = lo;
+    for (;;) {
+        // the first equation from `cur` on (cyclically) that is not finished and
+        // has tickets left, all threads looking at one equation each
+        __syncthreads();                // the previous equation's readers are done
+        if (threadIdx.x == 0) s_next = neq;
+        __syncthreads();
+        for (int k = threadIdx.x; k < neq; k += blockDim.x) {
+            int e = cur + k;
+            if (e >= neq) e -= neq;
+            const volatile DevFlags *f = bt.flags[e];
+            if (!f->done && (long long)f->ticket < bt.cum[e + 1] - bt.cum[e]) atomicMin(&s_next, k);
+        }
+        __syncthreads();
+        if (s_next >= neq) break;
+        int e = cur + s_next;
+        if (e >= neq) e -= neq;
+        cur = e;
+        const int *src = reinterpret_cast<const int *>(bt.sa[e]);
+        int *dst = reinterpret_cast<int *>(&sa);
+        for (int w = threadIdx.x; w < WORDS; w += blockDim.x) dst[w] = __ldg(src + w);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            sa.Y = bt.Y[e];
+            sa.cnt = bt.cnt[e];
+            sa.flags = bt.flags[e];
+        }
+        __syncthreads();
+        sweep_drain<real, RL>(sa, bt.far_split);
+    }
+}
+
+// Tile counters and ticket of every equation of a batched sweep.
+__global__ void k_sweep_init_batch(const __grid_constant__ SweepBatch bt) {
+    const int64_t total = bt.cum[bt.neq];
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = bt.neq - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) / 2;
+            if (bt.cum[mid] <= g) lo = mid;
+            else hi = mid - 1;
+        }
+        const SweepArgs *a = bt.sa[lo];
+        const int64_t tile = g - bt.cum[lo];
+        if (tile == 0) bt.flags[lo]->ticket = 0;
+        const int64_t rem = tile % a->ntiles1;
+        int c = 0;
+        for (int j = 0; j < a->Nm; ++j) {
+            const int Ij = (int)((rem / a->TS[j]) % a->Bc[j]);
+            c += (Ij < a->Bc[j] - 1);
+        }
+        bt.cnt[lo][tile] = c;
+    }
+}
+
 __global__ void k_sweep_init(const __grid_constant__ SweepArgs a) {
     if (blockIdx.x == 0 && threadIdx.x == 0) a.flags->ticket = 0;
     for (int64_t tile = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; tile < a.ntiles;
@@ -720,6 +805,43 @@ cudaError_t launch_sweep(int fp64, const SweepArgs &a, int grid, int threads, si
         k_sweep<float, false><<<grid, threads, smem, st>>>(a);
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_batch(int fp64, int real, const SweepBatch &b, int grid, int threads,
+                               size_t smem, cudaStream_t st) {
+    if (b.neq <= 0 || b.cum[b.neq] <= 0) return cudaSuccess;
+    int64_t blocks = (b.cum[b.neq] + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    k_sweep_init_batch<<<(unsigned)blocks, 256, 0, st>>>(b);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (real) {
+        if (fp64)
+            k_sweep_batch<double, true><<<grid, threads, smem, st>>>(b);
+        else
+            k_sweep_batch<float, true><<<grid, threads, smem, st>>>(b);
+    } else if (fp64) {
+        k_sweep_batch<double, false><<<grid, threads, smem, st>>>(b);
+    } else {
+        k_sweep_batch<float, false><<<grid, threads, smem, st>>>(b);
+    }
+    return cudaGetLastError();
+}
+
+int sweep_batch_blocks_per_sm(int fp64, int threads, size_t smem, int real) {
+    int nb = 0;
+    cudaError_t e;
+    if (real)
+        e = fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep_batch<double, true>,
+                                                                 threads, smem)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep_batch<float, true>,
+                                                                 threads, smem);
+    else
+        e = fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep_batch<double, false>,
+                                                                 threads, smem)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep_batch<float, false>,
+                                                                 threads, smem);
+    return e == cudaSuccess ? nb : 0;
 }
 
 cudaError_t launch_sweep_init(const SweepArgs &a, cudaStream_t st) {
@@ -832,8 +954,17 @@ cudaError_t sweep_init_attrs() {
         (e = cudaFuncSetAttribute(k_sweep<double, true>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess)
         return e;
-    return cudaFuncSetAttribute(k_sweep<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                big);
+    if ((e = cudaFuncSetAttribute(k_sweep<float, true>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_sweep_batch<double, false>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_sweep_batch<float, false>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_sweep_batch<double, true>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess)
+        return e;
+    return cudaFuncSetAttribute(k_sweep_batch<float, true>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, big);
 }
 
 }  // namespace sylv

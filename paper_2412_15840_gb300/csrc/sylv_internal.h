@@ -118,6 +118,21 @@ struct SweepArgs {
     const void *Vp[MAXM];
 };
 
+// Batched sweep over many equations in one persistent launch: each
+// equation's full sweep arguments (device copy owned by its plan) and the
+// call's tensor, tile counters and control block; cum[e] = tiles of the
+// equations before e.  Passed by value as the kernel parameter.
+constexpr int SWB_MAX = 512;
+struct SweepBatch {
+    int neq;
+    int far_split;
+    const SweepArgs *sa[SWB_MAX];
+    void *Y[SWB_MAX];
+    int *cnt[SWB_MAX];
+    DevFlags *flags[SWB_MAX];
+    long long cum[SWB_MAX + 1];
+};
+
 // Sweep of a plan whose T_j are all diagonal (every A_j normal, Remark 1):
 // y = c / (sigma + sum_j t_{j,i_j i_j}), Eq. (yi1i2iNdiag).  The leading
 // modes whose size product P1 is at most DIAG_HEAD_MAX share one table of
@@ -201,6 +216,9 @@ cudaError_t launch_modeprod(int fp64, int in_kind, int out_kind, int epi, const 
 cudaError_t launch_sweep(int fp64, const SweepArgs &a, int grid, int threads, size_t smem,
                          cudaStream_t st);
 cudaError_t launch_sweep_init(const SweepArgs &a, cudaStream_t st);
+cudaError_t launch_sweep_batch(int fp64, int real, const SweepBatch &b, int grid, int threads,
+                               size_t smem, cudaStream_t st);
+int sweep_batch_blocks_per_sm(int fp64, int threads, size_t smem, int real);
 cudaError_t launch_inv_table(int fp64, const SweepArgs &a, void *tab, int num_sms,
                              cudaStream_t st);
 cudaError_t launch_sweep_diag(int fp64, const DiagArgs &a, int num_sms, cudaStream_t st);
