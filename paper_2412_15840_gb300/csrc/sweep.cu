@@ -39,6 +39,7 @@
 #include <type_traits>
 
 #include "cplx.cuh"
+#include "sweep_common.cuh"
 #include "sylv_internal.h"
 
 namespace sylv {
@@ -51,30 +52,6 @@ constexpr int SW_OUT = 128;  // strip entries of the modes outside the tile appl
 // bound by the FP64 pipe; tiles of many small modes gain nothing)
 template <typename real> struct SwSub { static constexpr int value = 1; };
 template <> struct SwSub<float> { static constexpr int value = 4; };
-
-// The reciprocal of a diagonal sum is formed in FP64 in stage 1 and applied in
-// the in-tile wavefront: as double2 on the FP64 path; on the FP32 path as the
-// pair hi = fl32(1/den), lo = fl32(1/den - hi), so that the wavefront, which is
-// latency-critical, issues no instruction on GB300's narrow FP64 pipe.
-template <typename real> struct InvT;
-template <> struct InvT<double> { using type = double2; };
-template <> struct InvT<float> { using type = float4; };
-
-__device__ __forceinline__ void store_inv(double2 r, double2 &o) { o = r; }
-__device__ __forceinline__ void store_inv(double2 r, float4 &o) {
-    const float hx = (float)r.x, hy = (float)r.y;
-    o = make_float4(hx, hy, (float)(r.x - (double)hx), (float)(r.y - (double)hy));
-}
-__device__ __forceinline__ double2 apply_inv(double2 n, double2 v) {
-    return make_double2(n.x * v.x - n.y * v.y, n.x * v.y + n.y * v.x);
-}
-__device__ __forceinline__ float2 apply_inv(float2 n, float4 v) {
-    float tx = fmaf(n.x, v.z, -n.y * v.w);      // n * lo first, then n * hi
-    float ty = fmaf(n.x, v.w, n.y * v.z);
-    tx = fmaf(-n.y, v.y, tx);
-    ty = fmaf(n.y, v.x, ty);
-    return make_float2(fmaf(n.x, v.x, tx), fmaf(n.x, v.y, ty));
-}
 
 // Real-arithmetic variant (RL): C, Y and the strips are real (YT = real), the
 // tile itself is complex.  After the strips are subtracted, the tile's
@@ -149,7 +126,51 @@ __device__ __forceinline__ void rotate_pairs(const SweepArgs &a, C2 *tile_s, con
     }
 }
 
-// Every tile of one equation: take tickets from the equation's own counter
+// One group of RB rows of a fiber's strip update: acc[r] = -sum_c T[rg + r, c] y_c
+// over `ncol` columns (y in L2 at yp + c*Sj, T staged in shared memory with row
+// stride 1 and column stride bj), the H lanes of the fiber combined by
+// shuffles, and lane 0 of them adding the first `rows` accumulators to the
+// tile (rows <= RB; rows beyond `rows` read staged T entries of the next rows
+// of the block or zero padding and are not written).
+template <int RB, typename real, typename YT, typename C2>
+__device__ __forceinline__ void strip_group(const YT *yp, int64_t Sj, const YT *tc, int bj,
+                                            int ncol, int H, bool wr, C2 *dst, int bs, int rows) {
+    constexpr int UNR = sizeof(real) == 4 ? 8 : 4;   // strip loads in flight per thread
+    YT acc[RB];
+#pragma unroll
+    for (int r = 0; r < RB; ++r) acc[r] = YT{};
+    int c = 0;
+    for (; c + UNR <= ncol; c += UNR) {
+        YT y[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) y[u] = __ldcg(yp + u * Sj);
+        yp += UNR * Sj;
+#pragma unroll
+        for (int r = 0; r < RB; ++r) {
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) cmsub(acc[r], tc[u * bj + r], y[u]);
+        }
+        tc += UNR * bj;
+    }
+    for (; c < ncol; ++c) {
+        const YT y = __ldcg(yp);
+        yp += Sj;
+#pragma unroll
+        for (int r = 0; r < RB; ++r) cmsub(acc[r], tc[r], y);
+        tc += bj;
+    }
+    for (int o = 1; o < H; o <<= 1) {
+#pragma unroll
+        for (int r = 0; r < RB; ++r) shfl_add(acc[r], o);
+    }
+    if (wr) {
+#pragma unroll
+        for (int r = 0; r < RB; ++r)
+            if (r < rows) add_to(dst[r * bs], acc[r]);
+    }
+}
+
+// Every tile of one equation: take tickets from the equation's own counter// Every tile of one equation: take tickets from the equation's own counter
 // (a.flags->ticket) until they run out.  far_ok = 0 turns the far/near strip
 // split off (a batch of equations keeps the GPU busy without it).
 template <typename real, bool RL>
@@ -379,62 +400,20 @@ __device__ __forceinline__ void sweep_drain(const SweepArgs &a, const int far_ok
                     const YT *ybase = Y + g0 + (kend + k0 - oj + c0) * Sj;
                     const int ncol = c1 - c0;
                     for (int rg = 0; rg < bej; rg += SW_RG) {
-                        YT acc[SW_RG];
-#pragma unroll
-                        for (int r = 0; r < SW_RG; ++r) acc[r] = YT{};
-                        const YT *yp = ybase;
+                        // rows of this group: 1, 2, 4 or 8 accumulators, so that a
+                        // block of b_j = 1, 2, 4 rows issues no idle row's FMAs
+                        const int rows = min(SW_RG, bej - rg);
                         const YT *tc = Ts + rg + c0 * bj;
-                        int c = 0;
-                        // FP32: 8 strip loads in flight per thread (the loads are
-                        // latency-bound); FP64 keeps 4 (register budget)
-                        constexpr int UNR = sizeof(real) == 4 ? 8 : 4;
-                        for (; UNR == 8 && c + 8 <= ncol; c += 8) {
-                            YT y[8];
-#pragma unroll
-                            for (int u = 0; u < 8; ++u) y[u] = __ldcg(yp + u * Sj);
-                            yp += 8 * Sj;
-#pragma unroll
-                            for (int r = 0; r < SW_RG; ++r) {
-                                if (rg + r < bej) {
-#pragma unroll
-                                    for (int u = 0; u < 8; ++u) cmsub(acc[r], tc[u * bj + r], y[u]);
-                                }
-                            }
-                            tc += 8 * bj;
-                        }
-                        for (; c + 4 <= ncol; c += 4) {
-                            const YT y0 = __ldcg(yp), y1 = __ldcg(yp + Sj);
-                            const YT y2 = __ldcg(yp + 2 * Sj), y3 = __ldcg(yp + 3 * Sj);
-                            yp += 4 * Sj;
-#pragma unroll
-                            for (int r = 0; r < SW_RG; ++r) {
-                                if (rg + r < bej) {
-                                    cmsub(acc[r], tc[r], y0);
-                                    cmsub(acc[r], tc[bj + r], y1);
-                                    cmsub(acc[r], tc[2 * bj + r], y2);
-                                    cmsub(acc[r], tc[3 * bj + r], y3);
-                                }
-                            }
-                            tc += 4 * bj;
-                        }
-                        for (; c < ncol; ++c) {
-                            const YT y = __ldcg(yp);
-                            yp += Sj;
-#pragma unroll
-                            for (int r = 0; r < SW_RG; ++r)
-                                if (rg + r < bej) cmsub(acc[r], tc[r], y);
-                            tc += bj;
-                        }
-                        for (int o = 1; o < H; o <<= 1) {
-#pragma unroll
-                            for (int r = 0; r < SW_RG; ++r) shfl_add(acc[r], o);
-                        }
-                        if (ok && h == 0) {
-#pragma unroll
-                            for (int r = 0; r < SW_RG; ++r) {
-                                if (rg + r < bej) add_to(tile_s[e0 + (rg + r) * bs], acc[r]);
-                            }
-                        }
+                        C2 *dst = tile_s + e0 + rg * bs;
+                        const bool wr = ok && h == 0;
+                        if (rows == 1)
+                            strip_group<1, real>(ybase, Sj, tc, bj, ncol, H, wr, dst, bs, rows);
+                        else if (rows == 2)
+                            strip_group<2, real>(ybase, Sj, tc, bj, ncol, H, wr, dst, bs, rows);
+                        else if (rows <= 4)
+                            strip_group<4, real>(ybase, Sj, tc, bj, ncol, H, wr, dst, bs, rows);
+                        else
+                            strip_group<8, real>(ybase, Sj, tc, bj, ncol, H, wr, dst, bs, rows);
                     }
                 }
                 __syncthreads();
