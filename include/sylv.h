@@ -135,7 +135,10 @@ typedef struct {
                                  the triangular sweep of Eq. (yi1i2iN) */
     int32_t sweep_ctas_per_sm;  /* 0 = as many sweep CTAs per SM as fit; k > 0 caps it
                                  (fewer CTAs shorten each tile's latency) */
-    int32_t reserved[1];
+    int32_t tc_plain;         /* 1 = tensor-core transform passes without the TMA-fed
+                                 warp-specialised pipeline (0 = use it where it applies:
+                                 modes after the first with a stride that is a multiple
+                                 of 64 and n_j <= 64) */
 } sylv_tuning;
 
 /*

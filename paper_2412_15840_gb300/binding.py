@@ -80,7 +80,7 @@ class Tuning(ctypes.Structure):
                 ("sweep_threads", ctypes.c_int32), ("no_tensor_cores", ctypes.c_int32),
                 ("timeout_ms", ctypes.c_int32), ("fault_tile", ctypes.c_int32),
                 ("general_sweep", ctypes.c_int32), ("sweep_ctas_per_sm", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 1)]
+                ("tc_plain", ctypes.c_int32)]
 
 
 _LIB = None
@@ -267,7 +267,7 @@ class Plan:
                  block: Optional[Sequence[int]] = None, group_max: int = 0,
                  sweep_threads: int = 0, tensor_cores: bool = True, timeout_ms: int = 0,
                  fault_tile: int = 0, general_sweep: bool = False, sweep_ctas_per_sm: int = 0,
-                 real: bool = False):
+                 real: bool = False, tc_pipeline: bool = True):
         L = _lib()
         self.real = bool(real)
         if self.real and (A is None or Q is not None or T is not None):
@@ -296,7 +296,7 @@ class Plan:
         pT = ptrs(T) if T is not None else None
         tun = None
         if block is not None or group_max or sweep_threads or not tensor_cores or timeout_ms \
-                or fault_tile or general_sweep or sweep_ctas_per_sm:
+                or fault_tile or general_sweep or sweep_ctas_per_sm or not tc_pipeline:
             tun = Tuning()
             if block is not None:
                 for j, b in enumerate(block):
@@ -308,6 +308,7 @@ class Plan:
             tun.fault_tile = int(fault_tile)
             tun.general_sweep = int(bool(general_sweep))
             tun.sweep_ctas_per_sm = int(sweep_ctas_per_sm)
+            tun.tc_plain = 0 if tc_pipeline else 1
         h = vp()
         tp = ctypes.byref(tun) if tun is not None else None
         if self.real:

@@ -166,6 +166,7 @@ struct sylv_plan_s {
     std::vector<unsigned char> Eimg_host;      // staging of the exp(t A_j) digits
     std::vector<OzPass> ozpasses;
     bool oz = false;              // every mode qualifies: the residual runs on the tensor cores
+    bool tc_plain = false;        // tensor-core passes without the TMA-fed pipeline
 
     SweepConfig sweep;            // Y, T, diag, flags, counters filled per launch
     int64_t cnt_capacity = 0;     // tile counters the workspace holds (any tuned tiling)
@@ -733,9 +734,17 @@ cudaError_t run_groups(Ctx &c, const std::vector<Group> &gs, bool fp64, int whic
             t.L = g.L; t.R = g.R; t.tilesL = g.tilesL;
             t.flags = c.flags;
             t.done = done;
+            // TMA-fed warp-specialised pass where it applies, else the register-staged one
+            cudaError_t e = p->tc_plain ? cudaErrorNotSupported
+                                        : launch_modeprod_tcw(epi, t, p->num_sms, c.st);
+            if (e == cudaSuccess) {
+                count(c);
+                continue;
+            }
+            if (e != cudaErrorNotSupported) return e;
             const int64_t tiles = g.mode1 ? (g.R + 63) / 64 : (g.L * g.R + 63) / 64;
             const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, p->num_sms));
-            cudaError_t e = launch_modeprod_tc(epi, t, grid, g.smem, c.st);
+            e = launch_modeprod_tc(epi, t, grid, g.smem, c.st);
             if (e != cudaSuccess) return e;
             count(c);
             continue;
@@ -1466,6 +1475,7 @@ static sylv_status create_plan(sylv_plan_t *out, int N, const int64_t *n, int64_
     // transform and residual passes
     const int gmax = tuning ? tuning->group_max : 0;
     const bool allow_tc = !(tuning && tuning->no_tensor_cores);
+    p->tc_plain = tuning && tuning->tc_plain;
     sylv_status s = make_groups(*p, p->fp64(), true, gmax, allow_tc, p->tgroups);
     if (s != SYLV_OK) return s;
     s = make_groups(*p, true, false, gmax, false, p->rgroups);

@@ -646,6 +646,7 @@ cudaError_t kernels_init(int) {
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, big)) != cudaSuccess)
         return e;
     if ((e = modeprod_tc_init_attrs()) != cudaSuccess) return e;
+    if ((e = modeprod_tcw_init_attrs()) != cudaSuccess) return e;
     if ((e = resid_oz_init_attrs()) != cudaSuccess) return e;
     if ((e = modeprod_real_init_attrs()) != cudaSuccess) return e;
     return sweep_init_attrs();

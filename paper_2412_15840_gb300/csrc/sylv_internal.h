@@ -211,6 +211,10 @@ cudaError_t launch_maxabs(const void *x, int64_t count, DevFlags *flags, int num
 cudaError_t resid_oz_init_attrs();
 cudaError_t launch_modeprod_tc(int epi, const TCArgs &a, int grid, size_t smem, cudaStream_t st);
 cudaError_t modeprod_tc_init_attrs();
+// warp-specialised TMA-fed variant (modeprod_tcw.cu); cudaErrorNotSupported
+// when the pass does not qualify
+cudaError_t launch_modeprod_tcw(int epi, const TCArgs &a, int num_sms, cudaStream_t st);
+cudaError_t modeprod_tcw_init_attrs();
 cudaError_t launch_modeprod(int fp64, int in_kind, int out_kind, int epi, const MPArgs &a,
                             size_t smem, cudaStream_t st);
 cudaError_t launch_sweep(int fp64, const SweepArgs &a, int grid, int threads, size_t smem,
