@@ -350,6 +350,7 @@ typedef struct {
     int32_t sweep_inv_table;    /* 1: FP64 reciprocals read from the plan's table      */
     int32_t sweep_far_split;    /* 1: far strips applied ahead of the full wait        */
     int32_t sweep_block[64];    /* tile extent along each input mode (first N used)    */
+    int32_t sweep_lanes;        /* lanes per entry in the sweep's in-tile wavefront    */
 } sylv_plan_desc;
 sylv_status sylv_plan_describe(sylv_plan_t plan, sylv_plan_desc *out);
 

@@ -468,7 +468,7 @@ void fill_sweep_ptrs(const sylv_plan_s &p, SweepArgs &a, bool fp64) {
 // uploaded into a device buffer of its own, followed by a device copy of the
 // configuration's arguments.
 sylv_status build_sweep(const sylv_plan_s &p, const int *b, int threads, SweepConfig &cfg,
-                        int ctas_per_sm = 0) {
+                        int ctas_per_sm = 0, int sub = 0) {
     SweepArgs &a = cfg.a;
     a = SweepArgs{};
     a.Nm = p.Nm;
@@ -628,6 +628,10 @@ sylv_status build_sweep(const sylv_plan_s &p, const int *b, int threads, SweepCo
     // far strips ahead of the full dependency wait pay where the sweep is bound by
     // its dependency chain: at most two tiles per level for each resident CTA
     a.far_split = a.ntiles <= (int64_t)2 * cfg.grid * (maxlev + 1) ? 1 : 0;
+    // lanes per entry in the in-tile wavefront: 4 on the latency-bound FP32 path,
+    // else 1 (the FP64 path is bound by its pipe; a throughput-bound sweep by
+    // issue slots)
+    a.sub = sub > 0 ? sub : (!p.fp64() && a.far_split ? 4 : 1);
     SweepArgs full = a;
     fill_sweep_ptrs(p, full, p.fp64());
     if (cudaMemcpy(base + o_args, &full, sizeof(full), cudaMemcpyHostToDevice) != cudaSuccess)
@@ -1909,11 +1913,13 @@ sylv_status sylv_plan_autotune(sylv_plan_t p, void *Tdev, void *ws, size_t ws_by
         int b[MAXM];
         choose_blocks(*p, target, nullptr, b);
         if (tiles_for(*p, b) > p->cnt_capacity) continue;
-        for (int threads = 128; ok && threads <= 256; threads *= 2) {
+        for (int cand_i = 0; ok && cand_i < (p->fp64() ? 2 : 4); ++cand_i) {
+            const int threads = (cand_i & 1) ? 256 : 128;
+            const int sub = p->fp64() ? 1 : ((cand_i & 2) ? 4 : 1);
             int max_per = 0;
             for (int per = 0; ok && (per == 0 || per < max_per); ++per) {
                 SweepConfig cand;
-                if (build_sweep(*p, b, threads, cand, per) != SYLV_OK) {
+                if (build_sweep(*p, b, threads, cand, per, sub) != SYLV_OK) {
                     if (cand.dbuf) cudaFree(cand.dbuf);
                     break;
                 }
@@ -2170,6 +2176,7 @@ sylv_status sylv_plan_describe(sylv_plan_t p, sylv_plan_desc *out) {
     out->sweep_far_split = a.far_split;
     for (int j = 0, q = 0; j < p->N_in && j < 64; ++j)
         out->sweep_block[j] = (q < p->Nm && p->orig[q] == j) ? a.b[q++] : 1;
+    out->sweep_lanes = a.fast ? a.sub : 1;
     return SYLV_OK;
 }
 

@@ -47,11 +47,6 @@ namespace sylv {
 constexpr int SW_KCH = SWEEP_KCH;
 constexpr int SW_RG = 8;     // fiber rows kept in registers at once
 constexpr int SW_OUT = 128;  // strip entries of the modes outside the tile applied in stage 1a
-// lanes sharing one entry in the in-tile wavefront: 4 on the FP32 path with
-// packed coordinates (its wavefront is latency-bound), else 1 (the FP64 path is
-// bound by the FP64 pipe; tiles of many small modes gain nothing)
-template <typename real> struct SwSub { static constexpr int value = 1; };
-template <> struct SwSub<float> { static constexpr int value = 4; };
 
 // Real-arithmetic variant (RL): C, Y and the strips are real (YT = real), the
 // tile itself is complex.  After the strips are subtracted, the tile's
@@ -539,15 +534,18 @@ __device__ __forceinline__ void sweep_drain(const SweepArgs &a, const int far_ok
         if constexpr (RL) rotate_pairs(a, tile_s, s_be, s_o, true);
 
         // stage 2: in-tile wavefront over index sums measured from the tile's end.
-        // SW_SUB consecutive lanes share an entry: lane `sub` sums the in-tile
-        // successors along in-tile modes sub, sub + SW_SUB, ...; the partial
-        // sums are combined with shuffles and lane 0 of the group divides.
-        const int SW_SUB = a.fast ? SwSub<real>::value : 1;
+        // SW_SUB consecutive lanes share an entry (a.sub: 4 where the sweep is
+        // latency-bound, else 1, which issues fewer instructions): lane `sub`
+        // sums the in-tile successors along in-tile modes sub, sub + SW_SUB, ...;
+        // the partial sums are combined with shuffles and lane 0 of the group
+        // divides.
+        const int SW_LG = a.fast ? (a.sub >= 4 ? 2 : a.sub >= 2 ? 1 : 0) : 0;
+        const int SW_SUB = 1 << SW_LG;
         for (int lev = 0; lev < a.Lin; ++lev) {
             const int q0 = a.lev_start[lev], q1 = a.lev_start[lev + 1];
-            for (int base = q0; base < q1; base += nt / SW_SUB) {
-                const int qq = base + (int)threadIdx.x / SW_SUB;
-                const int sub = (int)threadIdx.x % SW_SUB;
+            for (int base = q0; base < q1; base += nt >> SW_LG) {
+                const int qq = base + ((int)threadIdx.x >> SW_LG);
+                const int sub = (int)threadIdx.x & (SW_SUB - 1);
                 bool act = qq < q1;
                 int e = 0;
                 unsigned long long c = 0;

@@ -113,6 +113,7 @@ struct SweepArgs {
     // pair of indices (2u, 2u + 1), identity where both are 1 x 1 blocks; null
     // for a mode without 2 x 2 blocks
     int far_split;            // strips beyond the successor block before the full wait
+    int sub;                  // lanes per entry in the in-tile wavefront (1, 2 or 4)
     int real;
     const void *Tr[MAXM];
     const void *Vp[MAXM];
