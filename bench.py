@@ -62,6 +62,8 @@ def parse():
                     help="skip the oracle error check and CPU baseline")
     ap.add_argument("--kernels-once", action="store_true",
                     help="run each hot-path kernel family once on the workload (for ncu)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the plans' default tilings (no sylv_plan_autotune)")
     ap.add_argument("--workloads", default="N3_n8,N29_n2,advdiff48,batch512,N7_n19",
                     help="other configurations measured in the default run (comma list; "
                          "'none' skips them)")
@@ -582,7 +584,7 @@ def run_workloads(args, dev, sampler):
         v.mul_(1.0 / np.sqrt(2.0))
         return torch.view_as_complex(v.view(total, 2))
 
-    def measure(name, probs, Bs, precs, steps, warmup, check):
+    def measure(name, probs, Bs, precs, steps, warmup, check, tune=False):
         rec = {}
         shapes = [p.shape for p in probs]
         ents = [p.n_tot * p.nrhs for p in probs]
@@ -595,6 +597,12 @@ def run_workloads(args, dev, sampler):
                           rtol=RTOL, max_refine=MAX_REFINE, device=dev.index)
                      for p, fa in zip(probs, facs)]
             setup = time.perf_counter() - t0
+            tuned = None
+            if tune and len(plans) == 1 and not args.no_autotune:
+                t1 = time.perf_counter()
+                blk, sweep_ms = plans[0].autotune()
+                tuned = {"sweep_block": list(blk), "sweep_ms": sweep_ms,
+                         "seconds": time.perf_counter() - t1}
             Xs = [torch.empty_like(b) for b in Bs]
             if len(plans) == 1:
                 ws = plans[0].workspace()
@@ -622,6 +630,7 @@ def run_workloads(args, dev, sampler):
             else:
                 infos = solve_batched(plans, Bs, Xs, ws, stream=stream, info=True)
             r = {"ms_per_solve": ms, "entries_per_s": entries / (ms * 1e-3), "setup_s": setup,
+                 "autotuned": tuned,
                  "status": sorted({i["status"] for i in infos}),
                  "refine_iters_max": max(i["refine_iters"] for i in infos)}
             if prec == "mixed_emu":
@@ -649,9 +658,11 @@ def run_workloads(args, dev, sampler):
             r["phase_roofline"] = phase_roofline(prec, ph, descs, shapes, ents, iters, hbm_gbs)
             d0 = descs[0]
             r["plan"] = {k: d0[k] for k in ("transform_passes", "transform_tc_passes",
+                                            "transform_tma", "transform_group_max",
                                             "residual_passes", "residual_tc", "diag_sweep",
                                             "sweep_block", "sweep_threads", "sweep_ctas_per_sm",
-                                            "sweep_tile_levels", "sweep_far_split")} \
+                                            "sweep_lanes", "sweep_tile_levels",
+                                            "sweep_far_split")} \
                 if len(plans) == 1 else {
                     "transform_tc_passes": sum(d["transform_tc_passes"] for d in descs),
                     "transform_passes": sum(d["transform_passes"] for d in descs),
@@ -687,14 +698,15 @@ def run_workloads(args, dev, sampler):
         chk = lambda prec, Xs: {"rel_err_vs_oracle": oracle.rel_err(
             from_device(Xs[0], p.B.shape), Xo)}
         res["N3_n8"] = {"config": "N=3, n_k=8 (512 entries), A=(randn+i randn)/sqrt(8)+3I, seed 0"}
-        res["N3_n8"].update(measure("N3_n8", [p], Bs, precs, K(20), W, chk))
+        res["N3_n8"].update(measure("N3_n8", [p], Bs, precs, K(20), W, chk, tune=True))
     if "N29_n2" in todo:
         p = si.binary_N29()
         Bd = to_device(p.B, device=dev)
         res["N29_n2"] = {"config": "N=29, n_j=2 except singleton modes 5, 17 ([1.5]); 2x2 "
                          "(randn+i randn)/sqrt(2)+2I; 2^27 entries; seed 0",
                          "error_check": "backward error at 1000 sampled entries"}
-        res["N29_n2"].update(measure("N29_n2", [p], [Bd], precs, K(10), W, eta_check(p, Bd)))
+        res["N29_n2"].update(measure("N29_n2", [p], [Bd], precs, K(10), W, eta_check(p, Bd),
+                                     tune=True))
         del Bd
     if "advdiff48" in todo:
         p = si.advdiff_n48()
@@ -710,7 +722,7 @@ def run_workloads(args, dev, sampler):
         res["advdiff48"] = {"config": "N=3, n=48 periodic advection-diffusion 0.01 D2 + 0.5 D1 "
                             "+ I (h = 2 pi/48), 32 RHS, seed 0; normal operators (Remark 1)",
                             "error_check": "FFT closed form (circulant operators)"}
-        res["advdiff48"].update(measure("advdiff48", [p], Bs, precs, K(20), W, chk))
+        res["advdiff48"].update(measure("advdiff48", [p], Bs, precs, K(20), W, chk, tune=True))
     if "batch512" in todo:
         rng, shapes = si.batch_shapes(512, 0)
         probs = [si.Problem(A=[si.gaussian_operator(rng, n, 3.0) for n in shp], B=None,
@@ -824,6 +836,15 @@ def main():
     t0 = time.perf_counter()
     fp64 = Plan(A=p.A, nrhs=1, prec="fp64", device=local)
     setup_s_fp64 = time.perf_counter() - t0
+    tuned = {}
+    if not args.no_autotune:
+        # tile extents, lanes, CTAs per SM and transform passes chosen by the
+        # library's autotuner on this GPU (outside the timed region)
+        for nm, pl in (("mixed", mixed), ("fp64", fp64)):
+            t1 = time.perf_counter()
+            blk, sweep_ms = pl.autotune()
+            tuned[nm] = {"sweep_block": list(blk), "sweep_ms": sweep_ms,
+                         "seconds": time.perf_counter() - t1}
     ws_m = mixed.workspace()
     ws_f = fp64.workspace()
     stream = torch.cuda.current_stream(dev)
@@ -881,6 +902,11 @@ def main():
     # --- supplementary: the residual's products on the bf16 tensor cores
     # (SYLV_MIXED_FP32_EMU; not the headline, which keeps the FP64 residual)
     emu = Plan(A=p.A, nrhs=1, prec="mixed_emu", rtol=RTOL, max_refine=MAX_REFINE, device=local)
+    if not args.no_autotune:
+        t1 = time.perf_counter()
+        blk, sweep_ms = emu.autotune()
+        tuned["mixed_emu"] = {"sweep_block": list(blk), "sweep_ms": sweep_ms,
+                              "seconds": time.perf_counter() - t1}
     ws_e = emu.workspace()
     Xe = torch.empty_like(B)
 
@@ -1031,9 +1057,9 @@ def main():
                                     [emu.describe()], [SHAPE], [entries], info_e["refine_iters"],
                                     hbm_gbs)}
     line["plans"] = {"mixed": mixed.describe(), "fp64": fp64.describe(),
-                     "mixed_emu": emu.describe()}
-    for d in line["plans"].values():
-        d["sweep_block"] = list(d["sweep_block"])
+                     "mixed_emu": emu.describe(), "autotuned": tuned or None}
+    for k in ("mixed", "fp64", "mixed_emu"):
+        line["plans"][k]["sweep_block"] = list(line["plans"][k]["sweep_block"])
     del X_mixed, X64, Xe, Bd, Xd, B, X
     torch.cuda.empty_cache()
     if world == 1 and args.workloads not in ("", "none"):

@@ -316,7 +316,11 @@ sylv_status sylv_sweep_static(sylv_plan_t plan, void *T_dev, void *stream);
 /*
  * sylv_plan_autotune -- measure candidate tilings of the triangular sweep on
  * this device (tile extents from ~64 to ~2048 entries, 128 or 256 threads
- * per CTA) for the plan's own shape and keep the fastest.  T_dev: scratch
+ * per CTA, 1 or 4 lanes per entry in the in-tile wavefront, each number of
+ * CTAs per SM) for the plan's own shape and keep the fastest; then the
+ * transform passes: the plan's tensor-core passes with or without the TMA
+ * pipeline, or CUDA-core passes only at several fusion widths of adjacent
+ * modes (one forward and one back transform timed per candidate).  T_dev: scratch
  * tensor in the plan's working precision (complex128 for SYLV_FP64, complex64
  * for SYLV_MIXED_FP32), overwritten with zeros and sweep results; workspace as
  * for sylv_solve.  The workspace size of the plan does not change.  On
@@ -351,6 +355,8 @@ typedef struct {
     int32_t sweep_far_split;    /* 1: far strips applied ahead of the full wait        */
     int32_t sweep_block[64];    /* tile extent along each input mode (first N used)    */
     int32_t sweep_lanes;        /* lanes per entry in the sweep's in-tile wavefront    */
+    int32_t transform_tma;      /* tensor-core passes fed by the TMA pipeline          */
+    int32_t transform_group_max;/* fusion width of the CUDA-core passes (0: automatic) */
 } sylv_plan_desc;
 sylv_status sylv_plan_describe(sylv_plan_t plan, sylv_plan_desc *out);
 

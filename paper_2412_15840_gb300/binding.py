@@ -73,7 +73,8 @@ class Desc(ctypes.Structure):
                 ("sweep_tiles", ctypes.c_int64), ("sweep_tile_entries", ctypes.c_int32),
                 ("sweep_tile_levels", ctypes.c_int32), ("sweep_inv_table", ctypes.c_int32),
                 ("sweep_far_split", ctypes.c_int32), ("sweep_block", ctypes.c_int32 * 64),
-                ("sweep_lanes", ctypes.c_int32)]
+                ("sweep_lanes", ctypes.c_int32), ("transform_tma", ctypes.c_int32),
+                ("transform_group_max", ctypes.c_int32)]
 
 
 class Tuning(ctypes.Structure):

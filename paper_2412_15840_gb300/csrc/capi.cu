@@ -167,6 +167,7 @@ struct sylv_plan_s {
     std::vector<OzPass> ozpasses;
     bool oz = false;              // every mode qualifies: the residual runs on the tensor cores
     bool tc_plain = false;        // tensor-core passes without the TMA-fed pipeline
+    int tgroup_max = 0;           // fusion width of the CUDA-core transform groups (0: automatic)
 
     SweepConfig sweep;            // Y, T, diag, flags, counters filled per launch
     int64_t cnt_capacity = 0;     // tile counters the workspace holds (any tuned tiling)
@@ -1018,7 +1019,7 @@ sylv_status solve_impl(sylv_plan_s *p, const void *B, void *X, void *ws, cudaStr
 // ------------------------------------------------------ batched graphs --
 // One CUDA graph per argument set of sylv_solve_batched: the equations'
 // launch sequences spread round-robin over a fork of up to 8 streams.
-constexpr int BATCH_STREAMS = 8;
+constexpr int BATCH_STREAMS = 32;
 constexpr size_t BATCH_CACHE = 16;
 
 struct BatchGraph {
@@ -1480,6 +1481,7 @@ static sylv_status create_plan(sylv_plan_t *out, int N, const int64_t *n, int64_
     const int gmax = tuning ? tuning->group_max : 0;
     const bool allow_tc = !(tuning && tuning->no_tensor_cores);
     p->tc_plain = tuning && tuning->tc_plain;
+    p->tgroup_max = gmax;
     sylv_status s = make_groups(*p, p->fp64(), true, gmax, allow_tc, p->tgroups);
     if (s != SYLV_OK) return s;
     s = make_groups(*p, true, false, gmax, false, p->rgroups);
@@ -1891,7 +1893,8 @@ sylv_status sylv_plan_autotune(sylv_plan_t p, void *Tdev, void *ws, size_t ws_by
         return SYLV_ERR_CUDA;
     auto time_cfg = [&](const SweepConfig &cfg, float &ms) -> bool {
         float best = 1e30f;
-        for (int rep = 0; rep < 3; ++rep) {          // first run warms up
+        int reps = 3;                                 // first run warms up
+        for (int rep = 0; rep < reps; ++rep) {
             if (launch_solve_init(c.flags, st) != cudaSuccess) return false;
             if (cudaEventRecord(e0, st) != cudaSuccess) return false;
             if ((p->diag_sweep ? run_sweep(c, Tdev, p->fp64())
@@ -1902,6 +1905,7 @@ sylv_status sylv_plan_autotune(sylv_plan_t p, void *Tdev, void *ws, size_t ws_by
             float t = 0.f;
             cudaEventElapsedTime(&t, e0, e1);
             if (rep > 0) best = std::min(best, t);
+            if (rep == 0 && t > 10.f) reps = 2;       // long sweeps: one timed run
         }
         ms = best;
         return true;
@@ -1916,14 +1920,22 @@ sylv_status sylv_plan_autotune(sylv_plan_t p, void *Tdev, void *ws, size_t ws_by
         for (int cand_i = 0; ok && cand_i < (p->fp64() ? 2 : 4); ++cand_i) {
             const int threads = (cand_i & 1) ? 256 : 128;
             const int sub = p->fp64() ? 1 : ((cand_i & 2) ? 4 : 1);
-            int max_per = 0;
-            for (int per = 0; ok && (per == 0 || per < max_per); ++per) {
+            // CTAs per SM: as many as fit, half of that, and 2 (fewer CTAs
+            // shorten each tile's latency on the dependency chain)
+            int pers[3] = {0, -1, -1};
+            for (int pi = 0; ok && pi < 3; ++pi) {
+                const int per = pers[pi];
+                if (per < 0) continue;
                 SweepConfig cand;
                 if (build_sweep(*p, b, threads, cand, per, sub) != SYLV_OK) {
                     if (cand.dbuf) cudaFree(cand.dbuf);
                     break;
                 }
-                if (per == 0) max_per = cand.per_sm;   // per = 0: as many as fit
+                if (pi == 0) {
+                    const int mx = cand.per_sm;
+                    if (mx / 2 >= 2 && mx / 2 < mx) pers[1] = mx / 2;
+                    if (mx > 2 && pers[1] != 2) pers[2] = 2;
+                }
                 float ms = 0.f;
                 if (!time_cfg(cand, ms)) {
                     ok = false;
@@ -1939,6 +1951,58 @@ sylv_status sylv_plan_autotune(sylv_plan_t p, void *Tdev, void *ws, size_t ws_by
                 }
             }
         }
+    }
+    // transform passes: the plan's tensor-core passes with or without the TMA
+    // pipeline, or CUDA-core passes only, at several fusion widths of adjacent
+    // modes; each candidate times one forward and one back transform in place
+    // on the scratch tensor
+    if (ok && p->Nm > 0) {
+        const int k = p->fp64() ? p->khi() : p->klo();
+        auto time_tf = [&](float &ms) -> bool {
+            float best = 1e30f;
+            for (int rep = 0; rep < 3; ++rep) {
+                if (cudaEventRecord(e0, st) != cudaSuccess) return false;
+                if (run_groups(c, p->tgroups, p->fp64(), 0, Tdev, k, Tdev, k, Tdev, k, EPI_STORE,
+                               nullptr) != cudaSuccess ||
+                    run_groups(c, p->tgroups, p->fp64(), 1, Tdev, k, Tdev, k, Tdev, k, EPI_STORE,
+                               nullptr) != cudaSuccess)
+                    return false;
+                if (cudaEventRecord(e1, st) != cudaSuccess) return false;
+                if (cudaEventSynchronize(e1) != cudaSuccess) return false;
+                float t = 0.f;
+                cudaEventElapsedTime(&t, e0, e1);
+                if (rep > 0) best = std::min(best, t);
+            }
+            ms = best;
+            return true;
+        };
+        const std::vector<Group> orig = p->tgroups;
+        const bool orig_plain = p->tc_plain;
+        const int orig_gmax = p->tgroup_max;
+        bool has_tc = false;
+        for (const auto &g : orig) has_tc |= g.tc != 0;
+        float best_ms = 1e30f;
+        std::vector<Group> best_g = orig;
+        bool best_plain = orig_plain;
+        int best_gmax = orig_gmax;
+        auto try_cand = [&](const std::vector<Group> &g, bool plain, int gm) {
+            p->tgroups = g;
+            p->tc_plain = plain;
+            float ms = 0.f;
+            if (!time_tf(ms)) { ok = false; return; }
+            if (ms < best_ms) { best_ms = ms; best_g = g; best_plain = plain; best_gmax = gm; }
+        };
+        try_cand(orig, orig_plain, orig_gmax);
+        if (ok && has_tc) try_cand(orig, !orig_plain, orig_gmax);
+        for (int gm : {0, 64, 256, 1024, 4096}) {
+            if (!ok) break;
+            std::vector<Group> g;
+            if (make_groups(*p, p->fp64(), true, gm, false, g) != SYLV_OK) continue;
+            try_cand(g, orig_plain, gm);
+        }
+        p->tgroups = ok ? best_g : orig;
+        p->tc_plain = ok ? best_plain : orig_plain;
+        p->tgroup_max = ok ? best_gmax : orig_gmax;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -2177,6 +2241,11 @@ sylv_status sylv_plan_describe(sylv_plan_t p, sylv_plan_desc *out) {
     for (int j = 0, q = 0; j < p->N_in && j < 64; ++j)
         out->sweep_block[j] = (q < p->Nm && p->orig[q] == j) ? a.b[q++] : 1;
     out->sweep_lanes = a.fast ? a.sub : 1;
+    out->transform_tma = 0;
+    for (const auto &g : p->tgroups)
+        if (g.tc && !g.mode1 && !p->tc_plain && g.L % 64 == 0 && g.P <= 64 && !g.cview)
+            out->transform_tma += 1;
+    out->transform_group_max = p->tgroup_max;
     return SYLV_OK;
 }
 
