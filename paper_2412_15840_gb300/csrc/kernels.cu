@@ -22,6 +22,10 @@ namespace sylv {
 // Transform pass
 // ---------------------------------------------------------------------------
 
+// tile entries loaded per thread before they are stored to shared memory
+// (independent loads in flight hide the HBM latency of the staging)
+constexpr int STAGE_U = 8;
+
 // two consecutive complex entries of a column-major matrix (16-byte aligned
 // when the first index is even)
 __device__ __forceinline__ void ldg_pair(const float2 *p, float2 &u, float2 &v) {
@@ -142,15 +146,30 @@ __global__ void __launch_bounds__(256) k_modeprod(const __grid_constant__ MPArgs
     const int rv = (int)((R - r0) < Rt ? (R - r0) : Rt);
     const Tin *in = reinterpret_cast<const Tin *>(a.in);
 
-    for (int t = threadIdx.x; t < E; t += blockDim.x) {
-        int l = t % Lt;
-        int rest = t / Lt;
-        int p = rest % P;
-        int r = rest / P;
-        C2 v = czero<C2>();
-        if (l < lv && r < rv) v = to_c(in[(l0 + l) + L * ((int64_t)p + a.P * (r0 + r))], real());
-        buf0[t] = v;
-        if (EPI == EPI_RESID && a.g3) reinterpret_cast<real *>(buf1)[t] = v.x + v.y;
+    // stage the tile: STAGE_U independent loads in flight per thread
+    for (int t0 = threadIdx.x; t0 < E; t0 += STAGE_U * blockDim.x) {
+        C2 v[STAGE_U];
+#pragma unroll
+        for (int u = 0; u < STAGE_U; ++u) {
+            const int t = t0 + u * blockDim.x;
+            v[u] = czero<C2>();
+            if (t < E) {
+                const int l = t % Lt;
+                const int rest = t / Lt;
+                const int p = rest % P;
+                const int r = rest / P;
+                if (l < lv && r < rv)
+                    v[u] = to_c(in[(l0 + l) + L * ((int64_t)p + a.P * (r0 + r))], real());
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < STAGE_U; ++u) {
+            const int t = t0 + u * blockDim.x;
+            if (t < E) {
+                buf0[t] = v[u];
+                if (EPI == EPI_RESID && a.g3) reinterpret_cast<real *>(buf1)[t] = v[u].x + v[u].y;
+            }
+        }
     }
     __syncthreads();
 
@@ -351,14 +370,25 @@ __global__ void __launch_bounds__(256) k_modeprod_n2(const __grid_constant__ MPA
 
     if (tid < 4 * G)
         Ms[tid >> 2][tid & 3] = __ldg(reinterpret_cast<const float2 *>(a.mats[tid >> 2]) + (tid & 3));
-    for (int t = tid; t < E; t += nt) {
-        const int l = t % Lt;
-        const int rest = t / Lt;
-        const int p = rest & (P - 1);
-        const int r = rest >> G;
-        float2 v = make_float2(0.f, 0.f);
-        if (l < lv && r < rv) v = to_c(in[(l0 + l) + L * ((int64_t)p + a.P * (r0 + r))], float());
-        buf[t] = v;
+    // stage the tile: STAGE_U independent loads in flight per thread
+    for (int t0 = tid; t0 < E; t0 += STAGE_U * nt) {
+        float2 v[STAGE_U];
+#pragma unroll
+        for (int u = 0; u < STAGE_U; ++u) {
+            const int t = t0 + u * nt;
+            v[u] = make_float2(0.f, 0.f);
+            if (t < E) {
+                const int l = t % Lt;
+                const int rest = t / Lt;
+                const int p = rest & (P - 1);
+                const int r = rest >> G;
+                if (l < lv && r < rv)
+                    v[u] = to_c(in[(l0 + l) + L * ((int64_t)p + a.P * (r0 + r))], float());
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < STAGE_U; ++u)
+            if (t0 + u * nt < E) buf[t0 + u * nt] = v[u];
     }
     __syncthreads();
 
@@ -426,7 +456,38 @@ __global__ void __launch_bounds__(256) k_modeprod_n2(const __grid_constant__ MPA
     }
 
     float nd = 0.f, nx = 0.f;
-    for (int t = tid; t < E; t += nt) {
+    if (EPI == EPI_ACCUM) {
+        // X += D: the X reads of STAGE_U entries issued together
+        for (int t0 = tid; t0 < E; t0 += STAGE_U * nt) {
+            int64_t gg[STAGE_U];
+            double2 xv[STAGE_U];
+#pragma unroll
+            for (int u = 0; u < STAGE_U; ++u) {
+                const int t = t0 + u * nt;
+                gg[u] = -1;
+                if (t < E) {
+                    const int l = t % Lt;
+                    const int rest = t / Lt;
+                    const int p = rest & (P - 1);
+                    const int r = rest >> G;
+                    if (l < lv && r < rv) gg[u] = (l0 + l) + L * ((int64_t)p + a.P * (r0 + r));
+                }
+                if (gg[u] >= 0) xv[u] = reinterpret_cast<const double2 *>(a.out)[gg[u]];
+            }
+#pragma unroll
+            for (int u = 0; u < STAGE_U; ++u) {
+                if (gg[u] < 0) continue;
+                const double2 dd = to_c(buf[t0 + u * nt], double());
+                double2 x = xv[u];
+                x.x += dd.x;
+                x.y += dd.y;
+                reinterpret_cast<double2 *>(a.out)[gg[u]] = x;
+                nd = fmaxf(nd, cabsmax(dd));
+                nx = fmaxf(nx, cabsmax(x));
+            }
+        }
+    }
+    for (int t = tid; EPI != EPI_ACCUM && t < E; t += nt) {
         const int l = t % Lt;
         const int rest = t / Lt;
         const int p = rest & (P - 1);
@@ -440,15 +501,6 @@ __global__ void __launch_bounds__(256) k_modeprod_n2(const __grid_constant__ MPA
             const double2 o = to_c(acc, double());
             reinterpret_cast<double2 *>(a.out)[g] = o;
             nx = fmaxf(nx, cabsmax(o));
-        } else if (EPI == EPI_ACCUM) {
-            double2 *Xp = reinterpret_cast<double2 *>(a.out);
-            double2 x = Xp[g];
-            const double2 dd = to_c(acc, double());
-            x.x += dd.x;
-            x.y += dd.y;
-            Xp[g] = x;
-            nd = fmaxf(nd, cabsmax(dd));
-            nx = fmaxf(nx, cabsmax(x));
         }
     }
     if (EPI == EPI_STORE_NORM || EPI == EPI_ACCUM) {
