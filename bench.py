@@ -785,6 +785,27 @@ def sampled_eta_dev(A, B_dev, X_dev, shape, nrhs, count=1000, seed=11):
                                      float(B_dev.abs().max().item()))
 
 
+def kernels_once_batch(local: int) -> int:
+    """One batched mixed solve of 64 equations drawn by the batched workload's
+    recipe (64 shape draws, seed 0, 4 RHS): the per-equation passes and one
+    k_sweep_batch launch per refinement step (a short sequence for ncu)."""
+    import torch
+    from paper_2412_15840_gb300.build import build
+    build()
+    from paper_2412_15840_gb300 import Plan, solve_batched, to_device, workspace_size_batched
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    probs = si.uneven_batch(64, 4, seed=0)
+    plans = [Plan(A=p.A, nrhs=4, prec="mixed", device=local) for p in probs]
+    Bs = [to_device(p.B, device=dev) for p in probs]
+    Xs = [torch.empty_like(b) for b in Bs]
+    ws = torch.empty(max(256, workspace_size_batched(plans)), dtype=torch.uint8, device=dev)
+    solve_batched(plans, Bs, Xs, ws)
+    torch.cuda.synchronize(dev)
+    print("kernels-once batch ok")
+    return 0
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -793,6 +814,8 @@ def main():
     if args.impl == "reference":
         return run_reference(args, rank, world)
     if args.kernels_once:
+        if args.workload == "batch512":
+            return kernels_once_batch(local)
         return kernels_once(local, small_n=args.workload == "n2_N29")
     if args.workload == "evolve_n64_N4":
         return evolve_workload(args, local)
