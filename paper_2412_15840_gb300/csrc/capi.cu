@@ -586,7 +586,8 @@ sylv_status build_sweep(const sylv_plan_s &p, const int *b, int threads, SweepCo
     a.tdsize = td;
     cfg.threads = threads;
     cfg.smem = (size_t)a.Pt * (esz + 16) + ((size_t)SWEEP_KCH * a.bmax + td) * esz +
-               (a.fast ? (size_t)a.Pt * 12 : 0);     // packed coordinates + schedule
+               (a.fast ? (size_t)a.Pt * 12 : 0) +    // packed coordinates + schedule
+               ((p.fp64() && !p.real) ? (size_t)SWEEP_KCH * a.bmax * 8 + 8 : 0);  // re + im plane
     if (cfg.smem > 200 * 1024) return SYLV_ERR_SHAPE;
 
     // device tables: order | sched | lev | sched_e | coord

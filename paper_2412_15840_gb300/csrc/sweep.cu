@@ -165,6 +165,68 @@ __device__ __forceinline__ void strip_group(const YT *yp, int64_t Sj, const YT *
     }
 }
 
+// FP64 complex rows by Gauss's three-multiplication product: with the staged
+// plane s = re + im of the T block and sx = re + im of each strip value (one
+// addition shared by the RB rows), sum_c T y = (sum tr yr - sum ti yi,
+// sum s sx - sum tr yr - sum ti yi): three FP64 FMAs per term instead of four,
+// on the FP64 pipe that bounds this sweep.
+template <int RB>
+__device__ __forceinline__ void strip_group3m(const double2 *yp, int64_t Sj, const double2 *tc,
+                                              const double *ts, int bj, int ncol, int H, bool wr,
+                                              double2 *dst, int bs, int rows) {
+    constexpr int UNR = 4;
+    double p1[RB], p2[RB], p3[RB];
+#pragma unroll
+    for (int r = 0; r < RB; ++r) p1[r] = p2[r] = p3[r] = 0.0;
+    int c = 0;
+    for (; c + UNR <= ncol; c += UNR) {
+        double2 y[UNR];
+        double sx[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) y[u] = __ldcg(yp + u * Sj);
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) sx[u] = y[u].x + y[u].y;
+        yp += UNR * Sj;
+#pragma unroll
+        for (int r = 0; r < RB; ++r) {
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                const double2 t = tc[u * bj + r];
+                p1[r] = fma(t.x, y[u].x, p1[r]);
+                p2[r] = fma(t.y, y[u].y, p2[r]);
+                p3[r] = fma(ts[u * bj + r], sx[u], p3[r]);
+            }
+        }
+        tc += UNR * bj;
+        ts += UNR * bj;
+    }
+    for (; c < ncol; ++c) {
+        const double2 y = __ldcg(yp);
+        const double sx = y.x + y.y;
+        yp += Sj;
+#pragma unroll
+        for (int r = 0; r < RB; ++r) {
+            p1[r] = fma(tc[r].x, y.x, p1[r]);
+            p2[r] = fma(tc[r].y, y.y, p2[r]);
+            p3[r] = fma(ts[r], sx, p3[r]);
+        }
+        tc += bj;
+        ts += bj;
+    }
+    double2 acc[RB];
+#pragma unroll
+    for (int r = 0; r < RB; ++r) acc[r] = make_double2(p2[r] - p1[r], (p1[r] + p2[r]) - p3[r]);
+    for (int o = 1; o < H; o <<= 1) {
+#pragma unroll
+        for (int r = 0; r < RB; ++r) shfl_add(acc[r], o);
+    }
+    if (wr) {
+#pragma unroll
+        for (int r = 0; r < RB; ++r)
+            if (r < rows) add_to(dst[r * bs], acc[r]);
+    }
+}
+
 // Every tile of one equation: take tickets from the equation's own counter// Every tile of one equation: take tickets from the equation's own counter
 // (a.flags->ticket) until they run out.  far_ok = 0 turns the far/near strip
 // split off (a batch of equations keeps the GPU busy without it).
@@ -182,6 +244,11 @@ __device__ __forceinline__ void sweep_drain(const SweepArgs &a, const int far_ok
     // once per CTA (every tile uses the same tables)
     unsigned long long *coord_s = reinterpret_cast<unsigned long long *>(Td + a.tdsize);
     int *sched_s = reinterpret_cast<int *>(coord_s + (a.fast ? a.Pt : 0));
+    // FP64 complex strips: the plane re + im of the staged T block (8-byte aligned
+    // after the schedule)
+    constexpr bool G3 = sizeof(real) == 8 && !RL;
+    double *Tsum = reinterpret_cast<double *>(
+        (reinterpret_cast<uintptr_t>(sched_s + (a.fast ? a.Pt : 0)) + 7) & ~(uintptr_t)7);
     __shared__ int s_ticket, s_tile, s_abort, s_full, s_hasfar;
     __shared__ int64_t s_o[MAXM];
     __shared__ int s_be[MAXM], s_cnt[MAXM], s_I[MAXM];
@@ -357,7 +424,9 @@ __device__ __forceinline__ void sweep_drain(const SweepArgs &a, const int far_ok
                 const int kk = min(SW_KCH, ce - k0);
                 for (int idx = threadIdx.x; idx < bej * kk; idx += nt) {
                     const int r = idx % bej, c = idx / bej;
-                    Ts[c * bj + r] = __ldg(Tj + (oj + r) + (kend + k0 + c) * nj);
+                    const YT t = __ldg(Tj + (oj + r) + (kend + k0 + c) * nj);
+                    Ts[c * bj + r] = t;
+                    if constexpr (G3) Tsum[c * bj + r] = t.x + t.y;
                 }
                 __syncthreads();
                 // H consecutive lanes share a fiber when the box has fewer fibers
@@ -401,7 +470,17 @@ __device__ __forceinline__ void sweep_drain(const SweepArgs &a, const int far_ok
                         const YT *tc = Ts + rg + c0 * bj;
                         C2 *dst = tile_s + e0 + rg * bs;
                         const bool wr = ok && h == 0;
-                        if (rows == 1)
+                        if constexpr (G3) {
+                            const double *tsp = Tsum + rg + c0 * bj;
+                            if (rows == 1)
+                                strip_group3m<1>(ybase, Sj, tc, tsp, bj, ncol, H, wr, dst, bs, rows);
+                            else if (rows == 2)
+                                strip_group3m<2>(ybase, Sj, tc, tsp, bj, ncol, H, wr, dst, bs, rows);
+                            else if (rows <= 4)
+                                strip_group3m<4>(ybase, Sj, tc, tsp, bj, ncol, H, wr, dst, bs, rows);
+                            else        // (eight rows of three sums exceed the register budget)
+                                strip_group<8, real>(ybase, Sj, tc, bj, ncol, H, wr, dst, bs, rows);
+                        } else if (rows == 1)
                             strip_group<1, real>(ybase, Sj, tc, bj, ncol, H, wr, dst, bs, rows);
                         else if (rows == 2)
                             strip_group<2, real>(ybase, Sj, tc, bj, ncol, H, wr, dst, bs, rows);
