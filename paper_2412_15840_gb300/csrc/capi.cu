@@ -586,9 +586,25 @@ sylv_status build_sweep(const sylv_plan_s &p, const int *b, int threads, SweepCo
     a.tdsize = td;
     cfg.threads = threads;
     cfg.smem = (size_t)a.Pt * (esz + 16) + ((size_t)SWEEP_KCH * a.bmax + td) * esz +
-               (a.fast ? (size_t)a.Pt * 12 : 0) +    // packed coordinates + schedule
-               ((p.fp64() && !p.real) ? (size_t)SWEEP_KCH * a.bmax * 8 + 8 : 0);  // re + im plane
+               (a.fast ? (size_t)a.Pt * 12 : 0);     // packed coordinates + schedule
     if (cfg.smem > 200 * 1024) return SYLV_ERR_SHAPE;
+    // FP64 complex strips by three multiplications need the re + im plane of the
+    // staged T block; it is reserved only where it costs no resident CTA, in the
+    // single-equation sweep and in the batched one (measured: a plane that took
+    // one CTA per SM slowed the 512-equation batch by 5%)
+    a.g3 = 0;
+    if (p.fp64() && !p.real) {
+        const size_t plane = (size_t)SWEEP_KCH * a.bmax * 8 + 8;
+        const int cap = ctas_per_sm > 0 ? ctas_per_sm : 1 << 20;
+        const int s0 = std::min(cap, sweep_blocks_per_sm(1, threads, cfg.smem, 0));
+        const int s1 = std::min(cap, sweep_blocks_per_sm(1, threads, cfg.smem + plane, 0));
+        const int b0 = sweep_batch_blocks_per_sm(1, threads, cfg.smem, 0);
+        const int b1 = sweep_batch_blocks_per_sm(1, threads, cfg.smem + plane, 0);
+        if (s1 >= s0 && s1 >= 1 && b1 >= b0 && cfg.smem + plane <= 200 * 1024) {
+            a.g3 = 1;
+            cfg.smem += plane;
+        }
+    }
 
     // device tables: order | sched | lev | sched_e | coord
     size_t o_order = 0;
@@ -2247,6 +2263,7 @@ sylv_status sylv_plan_describe(sylv_plan_t p, sylv_plan_desc *out) {
         if (g.tc && !g.mode1 && !p->tc_plain && g.L % 64 == 0 && g.P <= 64 && !g.cview)
             out->transform_tma += 1;
     out->transform_group_max = p->tgroup_max;
+    out->sweep_3m = a.g3;
     return SYLV_OK;
 }
 

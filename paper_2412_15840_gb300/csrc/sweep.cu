@@ -245,8 +245,9 @@ __device__ __forceinline__ void sweep_drain(const SweepArgs &a, const int far_ok
     unsigned long long *coord_s = reinterpret_cast<unsigned long long *>(Td + a.tdsize);
     int *sched_s = reinterpret_cast<int *>(coord_s + (a.fast ? a.Pt : 0));
     // FP64 complex strips: the plane re + im of the staged T block (8-byte aligned
-    // after the schedule)
-    constexpr bool G3 = sizeof(real) == 8 && !RL;
+    // after the schedule), present when the plan reserved it
+    constexpr bool C3 = sizeof(real) == 8 && !RL;
+    const bool G3 = C3 && a.g3;
     double *Tsum = reinterpret_cast<double *>(
         (reinterpret_cast<uintptr_t>(sched_s + (a.fast ? a.Pt : 0)) + 7) & ~(uintptr_t)7);
     __shared__ int s_ticket, s_tile, s_abort, s_full, s_hasfar;
@@ -426,7 +427,8 @@ __device__ __forceinline__ void sweep_drain(const SweepArgs &a, const int far_ok
                     const int r = idx % bej, c = idx / bej;
                     const YT t = __ldg(Tj + (oj + r) + (kend + k0 + c) * nj);
                     Ts[c * bj + r] = t;
-                    if constexpr (G3) Tsum[c * bj + r] = t.x + t.y;
+                    if constexpr (C3)
+                        if (G3) Tsum[c * bj + r] = t.x + t.y;
                 }
                 __syncthreads();
                 // H consecutive lanes share a fiber when the box has fewer fibers
@@ -470,17 +472,23 @@ __device__ __forceinline__ void sweep_drain(const SweepArgs &a, const int far_ok
                         const YT *tc = Ts + rg + c0 * bj;
                         C2 *dst = tile_s + e0 + rg * bs;
                         const bool wr = ok && h == 0;
-                        if constexpr (G3) {
-                            const double *tsp = Tsum + rg + c0 * bj;
-                            if (rows == 1)
-                                strip_group3m<1>(ybase, Sj, tc, tsp, bj, ncol, H, wr, dst, bs, rows);
-                            else if (rows == 2)
-                                strip_group3m<2>(ybase, Sj, tc, tsp, bj, ncol, H, wr, dst, bs, rows);
-                            else if (rows <= 4)
-                                strip_group3m<4>(ybase, Sj, tc, tsp, bj, ncol, H, wr, dst, bs, rows);
-                            else        // (eight rows of three sums exceed the register budget)
-                                strip_group<8, real>(ybase, Sj, tc, bj, ncol, H, wr, dst, bs, rows);
-                        } else if (rows == 1)
+                        // FP64 complex with the re + im plane: up to four rows by three
+                        // multiplications (eight rows of three sums exceed the registers)
+                        bool done = false;
+                        if constexpr (C3) {
+                            if (G3 && rows <= 4) {
+                                const double *tsp = Tsum + rg + c0 * bj;
+                                if (rows == 1)
+                                    strip_group3m<1>(ybase, Sj, tc, tsp, bj, ncol, H, wr, dst, bs, rows);
+                                else if (rows == 2)
+                                    strip_group3m<2>(ybase, Sj, tc, tsp, bj, ncol, H, wr, dst, bs, rows);
+                                else
+                                    strip_group3m<4>(ybase, Sj, tc, tsp, bj, ncol, H, wr, dst, bs, rows);
+                                done = true;
+                            }
+                        }
+                        if (done) continue;
+                        if (rows == 1)
                             strip_group<1, real>(ybase, Sj, tc, bj, ncol, H, wr, dst, bs, rows);
                         else if (rows == 2)
                             strip_group<2, real>(ybase, Sj, tc, bj, ncol, H, wr, dst, bs, rows);

@@ -114,6 +114,8 @@ struct SweepArgs {
     // for a mode without 2 x 2 blocks
     int far_split;            // strips beyond the successor block before the full wait
     int sub;                  // lanes per entry in the in-tile wavefront (1, 2 or 4)
+    int g3;                   // FP64 complex strips by three multiplications (re + im plane
+                              // of the staged T block in shared memory)
     int real;
     const void *Tr[MAXM];
     const void *Vp[MAXM];
