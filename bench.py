@@ -662,7 +662,8 @@ def run_workloads(args, dev, sampler):
                                             "residual_passes", "residual_tc", "diag_sweep",
                                             "sweep_block", "sweep_threads", "sweep_ctas_per_sm",
                                             "sweep_lanes", "sweep_tile_levels",
-                                            "sweep_far_split", "sweep_3m")} \
+                                            "sweep_far_split", "sweep_3m",
+                                            "transform_fib_passes")} \
                 if len(plans) == 1 else {
                     "transform_tc_passes": sum(d["transform_tc_passes"] for d in descs),
                     "transform_passes": sum(d["transform_passes"] for d in descs),

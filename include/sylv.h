@@ -358,6 +358,7 @@ typedef struct {
     int32_t transform_tma;      /* tensor-core passes fed by the TMA pipeline          */
     int32_t transform_group_max;/* fusion width of the CUDA-core passes (0: automatic) */
     int32_t sweep_3m;           /* 1: FP64 complex strips by three multiplications     */
+    int32_t transform_fib_passes;/* of the transform passes: one thread per fibre      */
 } sylv_plan_desc;
 sylv_status sylv_plan_describe(sylv_plan_t plan, sylv_plan_desc *out);
 

@@ -74,7 +74,8 @@ class Desc(ctypes.Structure):
                 ("sweep_tile_levels", ctypes.c_int32), ("sweep_inv_table", ctypes.c_int32),
                 ("sweep_far_split", ctypes.c_int32), ("sweep_block", ctypes.c_int32 * 64),
                 ("sweep_lanes", ctypes.c_int32), ("transform_tma", ctypes.c_int32),
-                ("transform_group_max", ctypes.c_int32), ("sweep_3m", ctypes.c_int32)]
+                ("transform_group_max", ctypes.c_int32), ("sweep_3m", ctypes.c_int32),
+                ("transform_fib_passes", ctypes.c_int32)]
 
 
 class Tuning(ctypes.Structure):

@@ -2,7 +2,7 @@
 
     python -m paper_2412_15840_gb300.build [--force] [--debug]
 
-Five translation units compiled in parallel (nvcc for the CUDA sources, the
+Translation units compiled in parallel (nvcc for the CUDA sources, the
 host C++ Schur code through nvcc's host compiler), one -gencode, static
 cudart, linked into paper_2412_15840_gb300/libsylv.so.  No cmake.
 """
@@ -20,7 +20,7 @@ LIB = os.path.join(PKG, "libsylv.so")
 BUILD = os.path.join(PKG, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["kernels.cu", "sweep.cu", "modeprod_tc.cu", "modeprod_tcw.cu", "resid_oz.cu", "real.cu", "capi.cu", "schur.cpp",
+SOURCES = ["kernels.cu", "sweep.cu", "modeprod_tc.cu", "modeprod_tcw.cu", "modeprod_fib.cu", "resid_oz.cu", "real.cu", "capi.cu", "schur.cpp",
            "schur_real.cpp", "expm.cpp"]
 HEADERS = ["sylv_internal.h", "cplx.cuh", "tc_ptx.cuh", "sweep_common.cuh", os.path.join("..", "..", "include", "sylv.h")]
 

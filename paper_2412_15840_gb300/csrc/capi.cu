@@ -41,6 +41,8 @@ struct Group {
     int cview = 0;
     // FP64 residual group: three-multiplication products (re + im plane staged)
     int g3 = 0;
+    // FP32 pass over one short mode, one thread per fibre (modeprod_fib.cu)
+    int fib = 0;
 };
 
 // A mode after the first runs on the tensor cores when its fibres are at least
@@ -370,11 +372,31 @@ sylv_status make_groups(const sylv_plan_s &p, bool fp64, bool composition, int g
         if (!p.real) return tc_mode_ok(p.S[jj], p.n[jj]);
         return p.S[jj] % 2 == 0 && tc_mode_ok(p.S[jj] / 2, p.n[jj]);
     };
+    // one-thread-per-fibre FP32 pass: complex modes with n <= FIB_NMAX outside
+    // the TMA-fed tensor-core pass (fibres 64-aligned along l), and not fused
+    // with a neighbour (checked below)
+    const bool use_fib = composition && !fp64 && !p.real;
+    auto tma_ok = [&](int jj) {
+        return tc_ok(jj) && jj > 0 && p.S[jj] % 64 == 0 && p.n[jj] <= 64;
+    };
+    auto fib_ok = [&](int jj) {
+        return use_fib && p.n[jj] >= 2 && p.n[jj] <= FIB_NMAX && !tma_ok(jj);
+    };
     int j = 0;
     while (j < p.Nm) {
         Group g;
         g.first = j;
         g.L = p.S[j];
+        if (fib_ok(j) && p.n[j] >= 16) {
+            g.count = 1;
+            g.P = p.n[j];
+            g.R = tot / (g.L * g.P);
+            g.fib = 1;
+            g.smem = (size_t)p.n[j] * fib_nx((int)p.n[j]) * 8;
+            out.push_back(g);
+            j += 1;
+            continue;
+        }
         const bool m1 = use_tc && !p.real && j == 0 && tc_mode1_ok(p.n[0], tot / p.n[0], p.Nm);
         if (m1 || tc_ok(j)) {
             g.count = 1;
@@ -398,6 +420,13 @@ sylv_status make_groups(const sylv_plan_s &p, bool fp64, bool composition, int g
                p.S[j + g.count] == g.L * g.P && !tc_ok(j + g.count))
             g.P *= p.n[j + g.count], g.count++;
         g.R = tot / (g.L * g.P);
+        if (g.count == 1 && fib_ok(j)) {      // not fused: one thread per fibre
+            g.fib = 1;
+            g.smem = (size_t)p.n[j] * fib_nx((int)p.n[j]) * 8;
+            out.push_back(g);
+            j += 1;
+            continue;
+        }
         if (!choose_tile(g.L, g.P, g.R, Et, Eh, g.Lt, g.Rt)) return SYLV_ERR_SHAPE;
         g.tilesL = (g.L + g.Lt - 1) / g.Lt;
         int64_t E = (int64_t)g.Lt * g.P * g.Rt;
@@ -732,6 +761,12 @@ cudaError_t run_groups(Ctx &c, const std::vector<Group> &gs, bool fp64, int whic
         int out_kind = last ? last_out_kind : work_kind;
         int epi = last ? last_epi : EPI_STORE;
         if (g.count == 0 && a.in == a.out && epi == EPI_STORE) continue;   // identity
+        if (g.fib) {
+            cudaError_t e = launch_modeprod_fib(in_kind, out_kind, epi, a, p->num_sms, c.st);
+            if (e != cudaSuccess) return e;
+            count(c);
+            continue;
+        }
         if (g.tc) {
             if (g.cview) {     // float32 / float64 tensors as complex64 / complex128 pairs
                 if (in_kind == ELEM_R32) in_kind = ELEM_C64;
@@ -2264,6 +2299,8 @@ sylv_status sylv_plan_describe(sylv_plan_t p, sylv_plan_desc *out) {
             out->transform_tma += 1;
     out->transform_group_max = p->tgroup_max;
     out->sweep_3m = a.g3;
+    out->transform_fib_passes = 0;
+    for (const auto &g : p->tgroups) out->transform_fib_passes += g.fib ? 1 : 0;
     return SYLV_OK;
 }
 

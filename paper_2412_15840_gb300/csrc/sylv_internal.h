@@ -15,6 +15,9 @@ namespace sylv {
 
 constexpr int MAXM = 40;   // modes with n_j > 1 (after singleton removal)
 constexpr int MAXG = 16;   // modes fused into one transform pass
+constexpr int FIB_NMAX = 24;  // longest fibre of the one-thread-per-fibre FP32 pass (at
+                              // n = 32 its 154 registers leave one CTA per SM, and the
+                              // tensor-core pass is faster: 32^5 forward 1.07 vs 1.27 ms)
 constexpr int MAX_N = 1024;
 constexpr int SWEEP_KCH = 64;  // columns of T_j staged per chunk by the sweep
 constexpr size_t INV_TABLE_MAX = (size_t)1 << 30;  // plan-resident reciprocal table budget
@@ -217,6 +220,10 @@ cudaError_t modeprod_tc_init_attrs();
 // warp-specialised TMA-fed variant (modeprod_tcw.cu); cudaErrorNotSupported
 // when the pass does not qualify
 cudaError_t launch_modeprod_tcw(int epi, const TCArgs &a, int num_sms, cudaStream_t st);
+// FP32 pass over one mode with n <= FIB_NMAX, one thread per fibre (modeprod_fib.cu)
+int fib_nx(int n);
+cudaError_t launch_modeprod_fib(int in_kind, int out_kind, int epi, const MPArgs &a, int num_sms,
+                                cudaStream_t st);
 cudaError_t modeprod_tcw_init_attrs();
 cudaError_t launch_modeprod(int fp64, int in_kind, int out_kind, int epi, const MPArgs &a,
                             size_t smem, cudaStream_t st);
