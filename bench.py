@@ -432,7 +432,7 @@ def real_workload(args, local: int) -> int:
     return 0
 
 
-def kernels_once(local: int, small_n: bool = False) -> int:
+def kernels_once(local: int, small_n: bool = False, n19: bool = False) -> int:
     """One launch group of every hot-path kernel family, in this order:
     FP64 residual passes, FP32 forward passes (first mode and modes 2-4 on
     the tensor cores), FP32 sweep, FP32 back passes, FP64 forward passes,
@@ -440,7 +440,10 @@ def kernels_once(local: int, small_n: bool = False) -> int:
     solve of the real-arithmetic variant on real operators of the same shape
     (a short, fixed launch sequence for ncu captures).  With --workload n2_N29:
     the same sequence (without the last two solves) on the n = 2 operators at
-    N = 25."""
+    N = 25.  With --workload n19_N7: the sequence up to the tensor-core-residual
+    solve on the n = 19 operators at N = 6 (19^6 = 47M entries: the FP32 passes
+    with one thread per fibre, the throughput-bound sweep, the emulated
+    residual at n = 19; a few GB on the device)."""
     import torch
     from paper_2412_15840_gb300.build import build
     build()
@@ -452,6 +455,8 @@ def kernels_once(local: int, small_n: bool = False) -> int:
         # singletons): the same kernels per entry as N = 29, few GB for ncu
         shape = tuple(1 if j in (4, 16) else 2 for j in range(25))
         p = si.random_problem(shape, 1, seed=0, shift=2.0, scale=1.0 / np.sqrt(2.0))
+    elif n19:
+        p = si.random_problem((19,) * 6, 1, seed=0, name="N6_n19")
     else:
         p = si.random_problem(SHAPE, 1, seed=0, name="N4_n64")
     m = Plan(A=p.A, nrhs=1, prec="mixed", device=local)
@@ -470,6 +475,7 @@ def kernels_once(local: int, small_n: bool = False) -> int:
         # one solve with the tensor-core residual (k_resid_oz passes)
         e = Plan(A=p.A, nrhs=1, prec="mixed_emu", device=local)
         e.solve(B, torch.empty_like(B))
+    if not small_n and not n19:
         # one mixed solve of the real-arithmetic variant (k_modeprod_r, the
         # tensor-core passes on the complex view, k_sweep<float, true>)
         q = si.real_cube_n64_N4()
@@ -817,7 +823,8 @@ def main():
     if args.kernels_once:
         if args.workload == "batch512":
             return kernels_once_batch(local)
-        return kernels_once(local, small_n=args.workload == "n2_N29")
+        return kernels_once(local, small_n=args.workload == "n2_N29",
+                            n19=args.workload == "n19_N7")
     if args.workload == "evolve_n64_N4":
         return evolve_workload(args, local)
     if args.workload == "real_n64_N4":

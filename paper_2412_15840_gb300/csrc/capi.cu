@@ -327,13 +327,15 @@ bool make_oz_passes(const sylv_plan_s &p, std::vector<sylv_plan_s::OzPass> &out)
         int cols = 32;
         while (cols < 4 * o.Np) cols *= 2;
         o.tmem_cols = cols;
-        // epilogue operand slots (4 per 32 columns, 16 B per thread and slot): in
-        // the X digit images, free while the epilogue runs, or appended
+        // epilogue operand slots (4 per 32 columns, 16 B per thread and slot):
+        // appended after the digit images where they fit (the K padding of the
+        // X images, zeroed once, then stays zero), else in the X digit images,
+        // free while the epilogue runs (the padding is zeroed again per tile)
         const size_t rstage = (size_t)4 * ((n + 31) / 32) * 512 * 16;
         const size_t xarea = (size_t)6 * o.ximg_bytes;
         o.rstage_off = 6 * o.aimg_bytes;
         o.smem = (size_t)6 * o.aimg_bytes + xarea + 4096;
-        if (rstage > xarea) {
+        if (rstage > xarea || o.smem + rstage <= (size_t)TC_SMEM_MAX) {
             o.rstage_off = (int)(o.smem);
             o.smem += rstage;
         }

@@ -230,10 +230,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_resid_oz(const __grid_constan
             if (e < 64 * n && p < pv) xv[b] = __ldg(Xg + gidx(r, p0, p, k));
         }
     };
+    // the epilogue's operand slots lie inside the X digit images (no room after them)
+    const bool rs_in_x = a.rstage_off < 6 * a.aimg_bytes + 6 * a.ximg_bytes;
     auto stage = [&]() {
-        // K padding (k >= n) of every digit image: zero (the epilogue's staging
-        // area may have overwritten it)
-        for (int w = tid; w < 6 * 128 * (Kp - n); w += OZ_THREADS) {
+        // K padding (k >= n) of every digit image: zero again when the epilogue's
+        // staging area may have overwritten it
+        for (int w = tid; rs_in_x && w < 6 * 128 * (Kp - n); w += OZ_THREADS) {
             const int img = w / (128 * (Kp - n)), rem = w - img * 128 * (Kp - n);
             const int row = rem & 127, k = n + (rem >> 7);
             *reinterpret_cast<uint16_t *>(Ximg + img * a.ximg_bytes +
