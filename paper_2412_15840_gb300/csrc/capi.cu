@@ -575,12 +575,21 @@ sylv_status build_sweep(const sylv_plan_s &p, const int *b, int threads, SweepCo
         }
         sched_e[qq] = e;
     }
+    // element offsets of the box positions from the tile's first entry (32-bit
+    // when the tensor per right-hand side is below 2^31 entries)
+    a.use_offs = a.fast && p.ntot < ((int64_t)1 << 31) ? 1 : 0;
+    std::vector<int> offs(a.use_offs ? a.Pt : 0, 0);
     if (a.fast)
         for (int e = 0; e < a.Pt; ++e) {
             unsigned long long c = 0;
-            for (int q = 0; q < a.nin; ++q)
-                c |= (unsigned long long)((e / a.BS[q]) % a.b[a.inmode[q]]) << a.cshift[q];
+            int64_t off = 0;
+            for (int q = 0; q < a.nin; ++q) {
+                const int t = (e / a.BS[q]) % a.b[a.inmode[q]];
+                c |= (unsigned long long)t << a.cshift[q];
+                off += (int64_t)t * a.S[a.inmode[q]];
+            }
             coord[e] = c;
+            if (a.use_offs) offs[(size_t)e] = (int)off;
         }
 
     // tile order: by level sum_j (Bc_j - 1 - I_j), then right-hand side, then id
@@ -617,7 +626,8 @@ sylv_status build_sweep(const sylv_plan_s &p, const int *b, int threads, SweepCo
     a.tdsize = td;
     cfg.threads = threads;
     cfg.smem = (size_t)a.Pt * (esz + 16) + ((size_t)SWEEP_KCH * a.bmax + td) * esz +
-               (a.fast ? (size_t)a.Pt * 12 : 0);     // packed coordinates + schedule
+               (a.fast ? (size_t)a.Pt * 12 : 0) +    // packed coordinates + schedule
+               (a.use_offs ? (size_t)a.Pt * 4 : 0);  // box offsets
     if (cfg.smem > 200 * 1024) return SYLV_ERR_SHAPE;
     // FP64 complex strips by three multiplications need the re + im plane of the
     // staged T block; it is reserved only where it costs no resident CTA, in the
@@ -637,13 +647,14 @@ sylv_status build_sweep(const sylv_plan_s &p, const int *b, int threads, SweepCo
         }
     }
 
-    // device tables: order | sched | lev | sched_e | coord
+    // device tables: order | sched | lev | sched_e | coord | offs
     size_t o_order = 0;
     size_t o_sched = align256(o_order + order.size() * 4);
     size_t o_lev = align256(o_sched + sched.size() * 4);
     size_t o_se = align256(o_lev + lev.size() * 4);
     size_t o_coord = align256(o_se + sched_e.size() * 4);
-    size_t o_args = align256(o_coord + coord.size() * 8);
+    size_t o_offs = align256(o_coord + coord.size() * 8);
+    size_t o_args = align256(o_offs + offs.size() * 4);
     size_t total = align256(o_args + sizeof(SweepArgs));
     std::vector<unsigned char> host(total, 0);
     std::memcpy(host.data() + o_order, order.data(), order.size() * 4);
@@ -651,6 +662,7 @@ sylv_status build_sweep(const sylv_plan_s &p, const int *b, int threads, SweepCo
     std::memcpy(host.data() + o_lev, lev.data(), lev.size() * 4);
     std::memcpy(host.data() + o_se, sched_e.data(), sched_e.size() * 4);
     std::memcpy(host.data() + o_coord, coord.data(), coord.size() * 8);
+    if (!offs.empty()) std::memcpy(host.data() + o_offs, offs.data(), offs.size() * 4);
     if (cudaMalloc(&cfg.dbuf, total) != cudaSuccess) {
         cudaGetLastError();
         cfg.dbuf = nullptr;
@@ -664,6 +676,7 @@ sylv_status build_sweep(const sylv_plan_s &p, const int *b, int threads, SweepCo
     a.lev_start = (const int *)(base + o_lev);
     a.sched_e = (const int *)(base + o_se);
     a.coord = (const unsigned long long *)(base + o_coord);
+    a.offs = (const int *)(base + o_offs);
     cfg.dargs = (const SweepArgs *)(base + o_args);
 
     // persistent grid: every SM holds as many tiles as fit, or the requested

@@ -244,12 +244,16 @@ __device__ __forceinline__ void sweep_drain(const SweepArgs &a, const int far_ok
     // once per CTA (every tile uses the same tables)
     unsigned long long *coord_s = reinterpret_cast<unsigned long long *>(Td + a.tdsize);
     int *sched_s = reinterpret_cast<int *>(coord_s + (a.fast ? a.Pt : 0));
+    // element offsets of the box positions (full tiles skip the decode of the
+    // packed coordinates)
+    int *offs_s = sched_s + (a.fast ? a.Pt : 0);
+    const bool offc = a.use_offs != 0;
     // FP64 complex strips: the plane re + im of the staged T block (8-byte aligned
-    // after the schedule), present when the plan reserved it
+    // after the offsets), present when the plan reserved it
     constexpr bool C3 = sizeof(real) == 8 && !RL;
     const bool G3 = C3 && a.g3;
     double *Tsum = reinterpret_cast<double *>(
-        (reinterpret_cast<uintptr_t>(sched_s + (a.fast ? a.Pt : 0)) + 7) & ~(uintptr_t)7);
+        (reinterpret_cast<uintptr_t>(offs_s + (offc ? a.Pt : 0)) + 7) & ~(uintptr_t)7);
     __shared__ int s_ticket, s_tile, s_abort, s_full, s_hasfar;
     __shared__ int64_t s_o[MAXM];
     __shared__ int s_be[MAXM], s_cnt[MAXM], s_I[MAXM];
@@ -268,6 +272,7 @@ __device__ __forceinline__ void sweep_drain(const SweepArgs &a, const int far_ok
         for (int e = threadIdx.x; e < a.Pt; e += nt) {
             coord_s[e] = a.coord[e];
             sched_s[e] = a.sched_e[e];
+            if (offc) offs_s[e] = a.offs[e];
         }
         // (the first __syncthreads of the tile loop orders these stores)
     }
@@ -285,13 +290,16 @@ __device__ __forceinline__ void sweep_drain(const SweepArgs &a, const int far_ok
 
         // tile geometry
         if (threadIdx.x == 0) {
-            const int64_t rhs = tile / a.ntiles1;
-            const int64_t rem = tile % a.ntiles1;
+            // tile ids, tile strides and block counts are below 2^31 (plan check):
+            // 32-bit divisions
+            const unsigned ut = (unsigned)tile, un1 = (unsigned)a.ntiles1;
+            const int64_t rhs = ut / un1;
+            const unsigned rem = ut - (unsigned)rhs * un1;
             int64_t gb = rhs * a.ntot;
             double dx = a.sig_re, dy = a.sig_im;
             int full = 1;
             for (int j = 0; j < Nm; ++j) {
-                const int Ij = (int)((rem / a.TS[j]) % a.Bc[j]);
+                const int Ij = (int)((rem / (unsigned)a.TS[j]) % (unsigned)a.Bc[j]);
                 const int64_t o = (int64_t)Ij * a.b[j];
                 int64_t be = a.n[j] - o;
                 if (be > a.b[j]) be = a.b[j];
@@ -354,7 +362,9 @@ __device__ __forceinline__ void sweep_drain(const SweepArgs &a, const int far_ok
             int64_t g = gbase;
             bool ok = true;
             double ex = s_den0x, ey = s_den0y;
-            if (fastc) {
+            if (offc && !partial && a.inv_tab) {
+                g += offs_s[e];
+            } else if (fastc) {
                 const unsigned long long c = coord_s[e];
                 for (int q = 0; q < nin; ++q) {
                     const int j = a.inmode[q];
@@ -444,7 +454,9 @@ __device__ __forceinline__ void sweep_drain(const SweepArgs &a, const int far_ok
                     const int e0 = (q >= 0) ? (f / bs) * (bs * bj) + (f % bs) : f;
                     int64_t g0 = gbase;
                     bool ok = f < F;
-                    if (ok && fastc) {
+                    if (ok && offc && !partial) {
+                        g0 += offs_s[e0];
+                    } else if (ok && fastc) {
                         const unsigned long long c = coord_s[e0];
                         for (int p = 0; p < nin; ++p) {
                             const int t = (int)((c >> a.cshift[p]) & a.cmask[p]);
@@ -583,7 +595,9 @@ __device__ __forceinline__ void sweep_drain(const SweepArgs &a, const int far_ok
             for (int e = threadIdx.x; e < a.Pt; e += nt) {
                 int64_t g = gbase;
                 bool ok = true;
-                if (fastc) {
+                if (offc && !partial) {
+                    g += offs_s[e];
+                } else if (fastc) {
                     const unsigned long long c = coord_s[e];
                     for (int q = 0; q < nin; ++q) {
                         const int t = (int)((c >> a.cshift[q]) & a.cmask[q]);
@@ -695,7 +709,9 @@ __device__ __forceinline__ void sweep_drain(const SweepArgs &a, const int far_ok
         for (int e = threadIdx.x; e < a.Pt; e += nt) {
             int64_t g = gbase;
             bool ok = true;
-            if (fastc) {
+            if (offc && !partial) {
+                g += offs_s[e];
+            } else if (fastc) {
                 const unsigned long long c = coord_s[e];
                 for (int p = 0; p < nin; ++p) {
                     const int t = (int)((c >> a.cshift[p]) & a.cmask[p]);

@@ -105,6 +105,9 @@ struct SweepArgs {
     const int *sched;         // in-tile schedule (a'-linear offsets by level)
     const int *sched_e;       // the same schedule as box offsets, for full tiles
     const unsigned long long *coord;  // per box offset: in-tile coordinates, 8 bits each
+    const int *offs;          // per box offset: element offset sum_q t_q S_q from the tile's
+                              // first entry (full tiles; when use_offs)
+    int use_offs;
     const int *lev_start;     // Lin + 1 entries
     long long timeout_cycles;
     int fault_tile;           // test hook: this tile never releases its predecessors (-1: none)
