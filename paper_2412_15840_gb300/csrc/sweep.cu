@@ -261,6 +261,9 @@ __device__ __forceinline__ void sweep_drain(const SweepArgs &a, const int far_ok
     // modes outside the tile (b_j = 1): the (offset, T value) pairs of their
     // strips, applied entry by entry in stage 1a without extra barriers
     __shared__ int s_npair, s_inlist[MAXM], s_pbase[MAXM];
+    // in-tile modes whose block is cut short in this tile (a partial tile's
+    // entries are valid when their coordinate is below s_be along these only)
+    __shared__ int s_npart, s_pq[MAXM];
     __shared__ int64_t s_pstride[SW_OUT];
     __shared__ YT s_pt[SW_OUT];
     __shared__ double s_den0x, s_den0y;
@@ -319,6 +322,10 @@ __device__ __forceinline__ void sweep_drain(const SweepArgs &a, const int far_ok
             s_den0x = dx;
             s_den0y = dy;
             s_full = full;
+            int npq = 0;
+            for (int q = 0; q < nin; ++q)
+                if (s_be[a.inmode[q]] < a.b[a.inmode[q]]) s_pq[npq++] = q;
+            s_npart = npq;
             int np = 0;
             for (int j = 0; j < Nm; ++j) {
                 s_inlist[j] = 0;
@@ -340,6 +347,14 @@ __device__ __forceinline__ void sweep_drain(const SweepArgs &a, const int far_ok
         // packed coordinates serve every tile; a partial tile (be_j < b_j for some
         // in-tile mode) skips the box offsets outside its valid extents
         const bool fastc = a.fast != 0, partial = s_full == 0;
+        // packed coordinates c of a box position inside this partial tile's extents
+        auto inside = [&](unsigned long long c) {
+            for (int k = 0; k < s_npart; ++k) {
+                const int q = s_pq[k];
+                if ((int)((c >> a.cshift[q]) & a.cmask[q]) >= s_be[a.inmode[q]]) return false;
+            }
+            return true;
+        };
         const int npair = s_npair;
         if (npair > 0) {
             for (int j = 0; j < Nm; ++j) {
@@ -362,7 +377,8 @@ __device__ __forceinline__ void sweep_drain(const SweepArgs &a, const int far_ok
             int64_t g = gbase;
             bool ok = true;
             double ex = s_den0x, ey = s_den0y;
-            if (offc && !partial && a.inv_tab) {
+            if (offc && a.inv_tab) {
+                ok = !partial || inside(coord_s[e]);
                 g += offs_s[e];
             } else if (fastc) {
                 const unsigned long long c = coord_s[e];
@@ -454,7 +470,8 @@ __device__ __forceinline__ void sweep_drain(const SweepArgs &a, const int far_ok
                     const int e0 = (q >= 0) ? (f / bs) * (bs * bj) + (f % bs) : f;
                     int64_t g0 = gbase;
                     bool ok = f < F;
-                    if (ok && offc && !partial) {
+                    if (ok && offc) {
+                        ok = !partial || inside(coord_s[e0]);
                         g0 += offs_s[e0];
                     } else if (ok && fastc) {
                         const unsigned long long c = coord_s[e0];
@@ -595,7 +612,8 @@ __device__ __forceinline__ void sweep_drain(const SweepArgs &a, const int far_ok
             for (int e = threadIdx.x; e < a.Pt; e += nt) {
                 int64_t g = gbase;
                 bool ok = true;
-                if (offc && !partial) {
+                if (offc) {
+                    ok = !partial || inside(coord_s[e]);
                     g += offs_s[e];
                 } else if (fastc) {
                     const unsigned long long c = coord_s[e];
@@ -654,10 +672,7 @@ __device__ __forceinline__ void sweep_drain(const SweepArgs &a, const int far_ok
                     if (fastc) {
                         e = sched_s[qq];
                         c = coord_s[e];
-                        if (partial)
-                            for (int p = 0; p < nin; ++p)
-                                if ((int)((c >> a.cshift[p]) & a.cmask[p]) >= s_be[a.inmode[p]])
-                                    act = false;
+                        if (partial && !inside(c)) act = false;
                     } else {
                         int r = a.sched[qq];
                         for (int p = 0; p < nin; ++p) {
@@ -709,7 +724,8 @@ __device__ __forceinline__ void sweep_drain(const SweepArgs &a, const int far_ok
         for (int e = threadIdx.x; e < a.Pt; e += nt) {
             int64_t g = gbase;
             bool ok = true;
-            if (offc && !partial) {
+            if (offc) {
+                ok = !partial || inside(coord_s[e]);
                 g += offs_s[e];
             } else if (fastc) {
                 const unsigned long long c = coord_s[e];
