@@ -659,6 +659,11 @@ def run_workloads(args, dev, sampler):
                 for k in ph:
                     ph[k] += t["ms"][k]
             r["phase_ms"] = ph
+            if len(plans) > 1:
+                r["phase_note"] = ("phase_ms sums the equations' phases from one solve with "
+                                   "phase timing on, which runs the equations one after another "
+                                   "outside the batched graph (single-equation sweeps); the "
+                                   "batched time is ms_per_solve")
             iters = r["refine_iters_max"] if prec != "fp64" else 0
             descs = [pl.describe() for pl in plans]
             r["phase_roofline"] = phase_roofline(prec, ph, descs, shapes, ents, iters, hbm_gbs)
