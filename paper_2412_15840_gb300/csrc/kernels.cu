@@ -184,6 +184,64 @@ __global__ void __launch_bounds__(256) k_modeprod(const __grid_constant__ MPArgs
         // (a.g3; the classical product remains for callers without the plane).
         const real *bufS = reinterpret_cast<const real *>(buf1);
         const bool g3 = a.g3 != 0;
+        if (G == 1 && g3 && a.rows4 && a.gn[0] >= 8) {
+            // one mode: a thread takes RES_RB consecutive rows i of one column (l, r),
+            // so every staged x value and its re + im sum feed RES_RB rows (rows past
+            // n are skipped); matrix entries are the same across the lanes of a warp
+            constexpr int RES_RB = 4;
+            const int nm = a.gn[0];
+            const C2 *M = reinterpret_cast<const C2 *>(a.mats[0]);
+            const real *MS = reinterpret_cast<const real *>(M + nm * nm);
+            const int ng = (nm + RES_RB - 1) / RES_RB;
+            const int W = Lt * ng * Rt;
+            for (int w = threadIdx.x; w < W; w += blockDim.x) {
+                const int l = w % Lt;
+                const int rest = w / Lt;
+                const int i0 = (rest % ng) * RES_RB;
+                const int r = rest / ng;
+                const int o = l + Lt * nm * r;                // tile index of (l, 0, r)
+                const C2 *src = buf0 + o;
+                const real *srcS = bufS + o;
+                real p1[RES_RB], p2[RES_RB], p3[RES_RB];
+#pragma unroll
+                for (int q = 0; q < RES_RB; ++q) p1[q] = p2[q] = p3[q] = 0;
+                for (int k = 0; k < nm; ++k) {
+                    const C2 x = src[k * Lt];
+                    const real xs = srcS[k * Lt];
+#pragma unroll
+                    for (int q = 0; q < RES_RB; ++q) {
+                        if (i0 + q >= nm) break;
+                        const C2 am = __ldg(M + (i0 + q) + k * nm);
+                        const real as = __ldg(MS + (i0 + q) + k * nm);
+                        p1[q] = fma(am.x, x.x, p1[q]);
+                        p2[q] = fma(am.y, x.y, p2[q]);
+                        p3[q] = fma(as, xs, p3[q]);
+                    }
+                }
+                if (l >= lv || r >= rv) continue;
+#pragma unroll
+                for (int q = 0; q < RES_RB; ++q) {
+                    const int i = i0 + q;
+                    if (i >= nm) break;
+                    const int64_t g = (l0 + l) + L * ((int64_t)i + a.P * (r0 + r));
+                    double2 *Rp = reinterpret_cast<double2 *>(a.out);
+                    double2 base;
+                    if (a.first) {
+                        const double2 b = reinterpret_cast<const double2 *>(a.B)[g];
+                        const double2 xv = to_c(buf0[o + i * Lt], double());
+                        base.x = b.x - (a.sig_re * xv.x - a.sig_im * xv.y);
+                        base.y = b.y - (a.sig_re * xv.y + a.sig_im * xv.x);
+                    } else {
+                        base = Rp[g];
+                    }
+                    double2 out;
+                    out.x = base.x - (double)(p1[q] - p2[q]);
+                    out.y = base.y - (double)((p3[q] - p1[q]) - p2[q]);
+                    Rp[g] = out;
+                }
+            }
+            return;
+        }
         for (int t = threadIdx.x; t < E; t += blockDim.x) {
             int l = t % Lt;
             int rest = t / Lt;

@@ -69,6 +69,8 @@ struct MPArgs {
     int first;
     int g3;                   // FP64 residual: three-multiplication products (re + im
                               // plane of X staged beside the tile); 0: classical
+    int rows4;                // FP64 residual of one mode: four rows per thread (a pass
+                              // with enough tiles to fill the GPU several times)
     // norms (float bits, max(|re|,|im|))
     DevFlags *flags;
     const int *done;          // early exit when *done != 0 (nullable)
