@@ -43,7 +43,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 
 # DRAM traffic per launch of the FP64 residual pass kernel, from an ncu capture
 # (see profiles/); valid only for the kernel source it was measured on.
-TRAFFIC = {"kernels_sha": "ddac781c8c7ef6a2", "bytes_per_launch": 764.3e6,
+TRAFFIC = {"kernels_sha": "5fe5f836f06544a9", "bytes_per_launch": 761.8e6,
            "source": "profiles/kernels_N4_n64.md (mean of the 4 residual-pass launches)"}
 
 
